@@ -1,0 +1,478 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: closed forms, textbook
+operators, brute-force real-space assemblies, library transforms and invariants.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gfp_oracle as O
+from paper_2009_03762_gb300 import microstructure as M
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FDD = ("F", "CD", "ACD", "HC", "AHC", "AFB_R", "R")
+
+
+# ----------------------------------------------------------------------------- transforms
+@pytest.mark.parametrize("disc", ["TD", "PCD"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 9])
+def test_dft_cardinality_and_unitarity(n, disc):
+    """F^+ and F^- are inverse (cardinality, App. A/B) and unitary."""
+    Fp, Fm = O.dft_matrices(n, 0.7, disc)
+    np.testing.assert_allclose(Fp.T @ Fm, np.eye(n), atol=1e-13)
+    np.testing.assert_allclose(Fm @ Fm.conj().T, np.eye(n), atol=1e-13)
+
+
+@pytest.mark.parametrize("disc", ["TD", "PCD"])
+def test_forward3_matches_numpy_fft(disc):
+    """The Rayleigh-product transform equals numpy's FFT up to the paper's ordering, scale and phase."""
+    rng = np.random.default_rng(0)
+    n3, n2, n1 = 5, 6, 4
+    f = rng.standard_normal((n3, n2, n1))
+    h = 1.0
+    mats = [O.dft_matrices(nr, h, disc) for nr in (n1, n2, n3)]
+    fc = O.forward3(f, mats)
+    ref = np.fft.fftshift(np.fft.fftn(f)) / np.sqrt(f.size)
+    if disc == "PCD":   # x_i^c = (i - 1/2) h adds e^{-i k h / 2} per axis
+        for ax, nr in zip((2, 1, 0), (n1, n2, n3)):
+            k = 2 * np.pi * O.kappa(nr) / (nr * h)
+            sh = [1, 1, 1]
+            sh[ax] = nr
+            ref = ref * np.exp(-0.5j * k * h).reshape(sh)
+    np.testing.assert_allclose(fc, ref, atol=1e-12)
+    np.testing.assert_allclose(O.inverse3(fc, mats).real, f, atol=1e-12)
+    # Parseval
+    assert abs(np.sum(np.abs(fc) ** 2) - np.sum(f ** 2)) < 1e-10
+
+
+# ----------------------------------------------------------------------------- symbols
+def _plane_wave(qvec, pts):
+    """e^{q . x} at points pts (..., 3) for a wave vector of imaginary wave numbers (x1, x2, x3)."""
+    return np.exp(pts[..., 0] * qvec[0] + pts[..., 1] * qvec[1] + pts[..., 2] * qvec[2])
+
+
+def _stencil_value(kind, r, qvec, x, h):
+    """Evaluate a difference operator of the paper on a plane wave directly from its definition.
+
+    kinds: FD, BD, CD, hC (eq. AppDifFinDFStn1D along axis r); AFD, ABD, ACD, AhC: the 3D
+    averages over the other two axes (eqs. FBDiff2D, BDDiff2D, CDDiff2D, hCDDiff2D generalised
+    to 3D as in eq. FreDifFinFBDF3D).
+    """
+    e = np.eye(3)
+    f = lambda p: _plane_wave(qvec, np.asarray(p, float))
+    def d1(kind1, p):
+        if kind1 == "FD":
+            return (f(p + h * e[r]) - f(p)) / h
+        if kind1 == "BD":
+            return (f(p) - f(p - h * e[r])) / h
+        if kind1 == "CD":
+            return (f(p + h * e[r]) - f(p - h * e[r])) / (2 * h)
+        if kind1 == "hC":
+            return (f(p + 0.5 * h * e[r]) - f(p - 0.5 * h * e[r])) / h
+    if kind in ("FD", "BD", "CD", "hC"):
+        return d1(kind, x)
+    s, t = (r + 1) % 3, (r + 2) % 3
+    if kind == "AFD":
+        offs = [a * e[s] + b * e[t] for a in (0, 1) for b in (0, 1)]
+        return np.mean([d1("FD", x + h * o) for o in offs])
+    if kind == "ABD":
+        offs = [a * e[s] + b * e[t] for a in (0, -1) for b in (0, -1)]
+        return np.mean([d1("BD", x + h * o) for o in offs])
+    if kind == "ACD":
+        offs = [a * e[s] + b * e[t] for a in (-1, 1) for b in (-1, 1)]
+        return np.mean([d1("CD", x + h * o) for o in offs])
+    if kind == "AhC":
+        offs = [a * e[s] + b * e[t] for a in (-0.5, 0.5) for b in (-0.5, 0.5)]
+        return np.mean([d1("hC", x + h * o) for o in offs])
+
+
+@pytest.mark.parametrize("scheme,a_kind,b_kind", [
+    ("F", None, None), ("CD", "CD", None), ("HC", "hC", None), ("ACD", "ACD", None),
+    ("AHC", "AhC", None), ("AFB_R", "AFD", "AhC")])
+def test_wave_vectors_are_stencil_symbols(scheme, a_kind, b_kind):
+    """q^a (and q^b) reproduce the real-space stencils applied to plane waves (modal forms)."""
+    n3, n2, n1 = 5, 6, 4
+    h = 1.3
+    qa, qb = O.wave_vectors(scheme, n3, n2, n1, h)
+    x0 = np.array([0.3, -1.1, 2.0])
+    ns = (n1, n2, n3)
+    for i3, i2, i1 in itertools.product(range(n3), range(n2), range(n1)):
+        idx = (i1, i2, i3)
+        qv = np.array([1j * 2 * np.pi * O.kappa(ns[r])[idx[r]] / (ns[r] * h) for r in range(3)])
+        f0 = _plane_wave(qv, x0)
+        for r in range(3):
+            if a_kind is None:
+                expect_a = qv[r]
+            else:
+                expect_a = _stencil_value(a_kind, r, qv, x0, h) / f0
+            assert abs(qa[r, i3, i2, i1] - expect_a) < 1e-11
+            if b_kind is not None:
+                expect_b = _stencil_value(b_kind, r, qv, x0, h) / f0
+                assert abs(qb[r, i3, i2, i1] - expect_b) < 1e-11
+            else:
+                assert abs(qb[r, i3, i2, i1] - np.conj(qa[r, i3, i2, i1])) < 1e-14
+
+
+def test_conjugate_afd_is_minus_abd():
+    """q^{AFD*} = -q^{ABD} (Sec. 5.3 after eq. EffNumWavConWil3D), checked on the ABD stencil."""
+    n3, n2, n1 = 4, 5, 6
+    qa, _ = O.wave_vectors("AFB_R", n3, n2, n1, 1.0)
+    ns = (n1, n2, n3)
+    x0 = np.zeros(3)
+    for i3, i2, i1 in itertools.product(range(n3), range(n2), range(n1)):
+        idx = (i1, i2, i3)
+        qv = np.array([1j * 2 * np.pi * O.kappa(ns[r])[idx[r]] / ns[r] for r in range(3)])
+        for r in range(3):
+            abd = _stencil_value("ABD", r, qv, x0, 1.0)
+            assert abs(np.conj(qa[r, i3, i2, i1]) + abd) < 1e-12
+
+
+def test_willot_qw_equals_qfd_except_limit():
+    """q^W = q^FD for mu = 2..n and lim_{mu->1} q^W = q^FD (Sec. 5.3, eq. FreDifFinFBDFR3D)."""
+    for n in (6, 8, 11):
+        q = O.q_fourier(n, 1.0)
+        np.testing.assert_allclose(O.q1d("W", q, 1.0), O.q1d("FD", q, 1.0), atol=1e-13)
+    # the limit itself: q h -> -i pi
+    t = -np.pi + 1e-6
+    qw = np.tanh(0.5j * t) * (np.exp(1j * t) + 1.0)
+    assert abs(qw - (np.exp(-1j * np.pi) - 1.0)) < 1e-5
+    qa_afb, _ = O.wave_vectors("AFB_R", 6, 6, 6, 1.0)
+    qa_r, _ = O.wave_vectors("R", 6, 6, 6, 1.0)
+    np.testing.assert_allclose(qa_afb, qa_r, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- Green operator
+def _C_apply(lam, mu, A):
+    return O.stiffness_apply(lam, mu, A)
+
+
+@pytest.mark.parametrize("scheme", FDD)
+def test_gamma_projection_and_idempotence(scheme):
+    """Gamma C_H sym(u (x) q^a) = sym(u (x) q^a) and Gamma C_H Gamma = Gamma (from eq. EquMecFunGre3D)."""
+    rng = np.random.default_rng(1)
+    n3, n2, n1 = 5, 4, 6
+    lam_h, mu_h = 1.7, 0.9
+    qa, qb = O.wave_vectors(scheme, n3, n2, n1)
+    G = O.green(qa, qb, lam_h, mu_h)
+    u = rng.standard_normal((3, n3, n2, n1)) + 1j * rng.standard_normal((3, n3, n2, n1))
+    eps = O.sym_outer(u, qa)
+    live = np.abs(np.sum(qa * qb, axis=0)) > 0
+    back = O.gamma_apply(G, qa, qb, _C_apply(lam_h, mu_h, eps))
+    np.testing.assert_allclose(back[:, :, live], eps[:, :, live], atol=1e-12)
+    A = rng.standard_normal((3, 3, n3, n2, n1)) + 1j * rng.standard_normal((3, 3, n3, n2, n1))
+    A = 0.5 * (A + np.swapaxes(A, 0, 1))
+    GA = O.gamma_apply(G, qa, qb, A)
+    GCGA = O.gamma_apply(G, qa, qb, _C_apply(lam_h, mu_h, GA))
+    np.testing.assert_allclose(GCGA, GA, atol=1e-12)
+    k0 = (n3 // 2, n2 // 2, n1 // 2)
+    assert np.all(GA[(slice(None), slice(None)) + k0] == 0)
+
+
+@pytest.mark.parametrize("scheme", FDD)
+def test_gamma_real_and_even(scheme):
+    """The literal complex Gamma of every pairing is real and even in k (interior modes)."""
+    n = 7
+    lam_h, mu_h = 1.2, 0.8
+    qa, qb = O.wave_vectors(scheme, n, n, n)
+    G = O.green(qa, qb, lam_h, mu_h)
+    mats = []
+    for (i, j) in O.VOIGT:
+        B = np.zeros((3, 3, n, n, n))
+        B[i, j] = 1.0
+        B[j, i] = 1.0
+        mats.append(O.gamma_apply(G, qa, qb, B))
+    mats = np.array(mats)
+    assert np.abs(mats.imag).max() < 1e-13
+    # kappa -> -kappa is index m+kappa -> m-kappa; for odd n the range is symmetric
+    flipped = mats[..., ::-1, ::-1, ::-1]
+    np.testing.assert_allclose(mats.real, flipped.real, atol=1e-13)
+
+
+def test_gamma_fourier_is_textbook_isotropic_operator():
+    """For the plain Fourier scheme Gamma equals the isotropic Gamma^0 of Moulinec-Suquet (1998):
+    Gamma_khij = (d_ki x_h x_j + d_hi x_k x_j + d_kj x_h x_i + d_hj x_k x_i)/(4 mu |x|^2)
+                 - (lam + mu)/(mu (lam + 2 mu)) x_i x_j x_k x_h / |x|^4."""
+    n = 5
+    lam_h, mu_h = 2.3, 0.7
+    qa, qb = O.wave_vectors("F", n, n, n)
+    G = O.green(qa, qb, lam_h, mu_h)
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((3, 3, n, n, n))
+    A = 0.5 * (A + np.swapaxes(A, 0, 1))
+    got = O.gamma_apply(G, qa, qb, A).real
+    xi = (qa / 1j).real
+    d = np.eye(3)
+    x2 = np.sum(xi * xi, axis=0)
+    x2s = np.where(x2 > 0, x2, 1.0)
+    c = (lam_h + mu_h) / (mu_h * (lam_h + 2 * mu_h))
+    ref = np.zeros_like(got)
+    for k, h_, i, j in itertools.product(range(3), repeat=4):
+        g = ((d[k, i] * xi[h_] * xi[j] + d[h_, i] * xi[k] * xi[j] + d[k, j] * xi[h_] * xi[i]
+              + d[h_, j] * xi[k] * xi[i]) / (4 * mu_h * x2s)
+             - c * xi[i] * xi[j] * xi[k] * xi[h_] / x2s ** 2)
+        ref[k, h_] += g * A[i, j]
+    ref[:, :, x2 == 0] = 0.0
+    np.testing.assert_allclose(got, ref, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- whole solver
+@pytest.mark.parametrize("scheme", FDD + ("DGO",))
+def test_homogeneous_medium_converges_in_one_iteration(scheme):
+    n = 4
+    lam = np.full((n, n, n), 2.5)
+    mu = np.full((n, n, n), 1.1)
+    E = np.array([0.01, -0.02, 0.005, 0.003, -0.004, 0.002])
+    r = O.solve(lam, mu, scheme, E, tol=1e-12, ref=(1.0, 0.5))
+    assert r.iters == 1
+    np.testing.assert_allclose(r.eps, E[:, None, None, None] * np.ones((1, n, n, n)), atol=1e-15)
+
+
+def _laminate_closed_form(lam1, mu1, E):
+    """Exact mean stress of a laminate along x1 (T constant across the layers, Sec. 2.1
+    generalised: sigma_11, sigma_12, sigma_13 uniform; eps_22, eps_33, eps_23 uniform)."""
+    E11, E22, E33, E23, E13, E12 = E
+    M_ = lam1 + 2 * mu1
+    s11 = (E11 + np.mean(lam1 / M_) * (E22 + E33)) / np.mean(1.0 / M_)
+    s12 = E12 / np.mean(1.0 / (2 * mu1))
+    s13 = E13 / np.mean(1.0 / (2 * mu1))
+    e11 = (s11 - lam1 * (E22 + E33)) / M_
+    tr = e11 + E22 + E33
+    s22 = np.mean(lam1 * tr + 2 * mu1 * E22)
+    s33 = np.mean(lam1 * tr + 2 * mu1 * E33)
+    s23 = np.mean(2 * mu1 * E23)
+    return np.array([s11, s22, s33, s23, s13, s12]), e11
+
+
+@pytest.mark.parametrize("scheme,n1", [("F", 7), ("F", 8), ("HC", 8), ("AHC", 8), ("AFB_R", 8),
+                                      ("R", 6), ("CD", 7), ("ACD", 7), ("DGO", 6)])
+def test_laminate_exact_effective_response(scheme, n1):
+    lam, mu = M.random_laminate(n1, 3, 4, seed=5)
+    E = np.array([0.01, -0.004, 0.007, 0.003, -0.002, 0.005])
+    # the DGO's stress form has equilibrium as its fixed point; its polarization form is pinned below
+    kw = dict(dgo_form="stress") if scheme == "DGO" else {}
+    r = O.solve(lam, mu, scheme, E, tol=1e-12, maxit=3000, **kw)
+    assert r.converged
+    ref, e11 = _laminate_closed_form(lam[0, 0], mu[0, 0], E)
+    np.testing.assert_allclose(r.sigma_mean, ref, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(r.eps[0], np.broadcast_to(e11, r.eps[0].shape), rtol=1e-8, atol=1e-12)
+
+
+def _load_golden_1d():
+    rows = np.loadtxt(os.path.join(HERE, "golden", "mi1d_sharp.txt"))
+    out = {}
+    for n in (10, 50, 90):
+        sel = rows[rows[:, 0] == n]
+        out[n] = (sel[:, 2], sel[:, 3])
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["F", "HC", "AHC", "AFB_R", "R"])
+def test_1d_matrix_inclusion_matches_paper_closed_form(scheme):
+    """1D MI example of Sec. 4 (n = 10, 50, 90): all these wave numbers give the nodal closed form."""
+    gold = _load_golden_1d()
+    for n, (nu, E_ref) in gold.items():
+        C = 1.0 + 99.0 * nu
+        lam = np.zeros((1, 1, n))
+        mu = (0.5 * C).reshape(1, 1, n)
+        r = O.solve(lam, mu, scheme, [1.0, 0, 0, 0, 0, 0], tol=1e-11, maxit=2000)
+        assert r.converged
+        np.testing.assert_allclose(r.eps[0, 0, 0], E_ref, rtol=1e-10)
+
+
+def test_td_and_pcd_fdd_give_identical_iterates():
+    """Algorithm P on the same sampled moduli equals Algorithm T ("independent of s", Sec. 3.2)."""
+    lam, mu = M.random_field(6, 5, 4, seed=2)
+    for scheme in ("F", "AFB_R", "ACD"):
+        a = O.solve(lam, mu, scheme, [0.01, 0, 0, 0.002, 0, 0], tol=1e-10, disc="TD")
+        b = O.solve(lam, mu, scheme, [0.01, 0, 0, 0.002, 0, 0], tol=1e-10, disc="PCD")
+        assert a.iters == b.iters
+        np.testing.assert_allclose(a.eps, b.eps, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- dense real-space solves
+def _shift(n3, n2, n1, d):
+    """Periodic shift matrix S with (S f)[x] = f[x + d] on the flattened (n3, n2, n1) grid."""
+    N = n1 * n2 * n3
+    idx = np.arange(N).reshape(n3, n2, n1)
+    src = np.roll(idx, shift=(-d[2], -d[1], -d[0]), axis=(0, 1, 2)).ravel()
+    S = np.zeros((N, N))
+    S[np.arange(N), src] = 1.0
+    return S
+
+
+def _stencil_matrices(kind, n3, n2, n1):
+    """Real-space difference matrices D_r (r = x1, x2, x3) of the paper's stencils, h = 1."""
+    e = np.eye(3, dtype=int)
+    Sh = lambda d: _shift(n3, n2, n1, tuple(int(v) for v in d))
+    mats = []
+    for r in range(3):
+        s, t = (r + 1) % 3, (r + 2) % 3
+        if kind == "CD":
+            D = 0.5 * (Sh(e[r]) - Sh(-e[r]))
+        elif kind == "ACD":
+            D = sum(0.125 * (Sh(e[r] + a * e[s] + b * e[t]) - Sh(-e[r] + a * e[s] + b * e[t]))
+                    for a in (-1, 1) for b in (-1, 1))
+        elif kind == "AFD":
+            D = sum(0.25 * (Sh(e[r] + a * e[s] + b * e[t]) - Sh(a * e[s] + b * e[t]))
+                    for a in (0, 1) for b in (0, 1))
+        elif kind == "ABD":
+            D = sum(0.25 * (Sh(a * e[s] + b * e[t]) - Sh(-e[r] + a * e[s] + b * e[t]))
+                    for a in (0, -1) for b in (0, -1))
+        mats.append(D)
+    return mats
+
+
+def _fourier_diff_matrices(n):
+    """Textbook periodic spectral differentiation matrix for odd n on [0, n) (Trefethen 2000, ch. 3):
+    D_ij = (pi/n) (-1)^{i-j} / sin(pi (i-j)/n), D_ii = 0."""
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                D[i, j] = (np.pi / n) * (-1.0) ** (i - j) / np.sin(np.pi * (i - j) / n)
+    I = np.eye(n)
+    return [np.kron(I, np.kron(I, D)), np.kron(I, np.kron(D, I)), np.kron(D, np.kron(I, I))]
+
+
+def _dense_equilibrium_strain(lam, mu, E, grad, div):
+    """Solve div_b C (E_bar + sym grad_a u) = 0 for u (minimum-norm least squares), return eps."""
+    N = lam.size
+    l = lam.ravel()
+    m_ = mu.ravel()
+
+    def strain_from_u(U):          # U: (3N, cols)
+        cols = U.shape[1]
+        u = U.reshape(3, N, cols)
+        H = np.array([[grad[j] @ u[i] for j in range(3)] for i in range(3)])   # H_ij = d_j u_i
+        return 0.5 * (H + np.swapaxes(H, 0, 1))
+
+    def stress(eps):
+        tr = eps[0, 0] + eps[1, 1] + eps[2, 2]
+        s = 2 * m_[:, None] * eps
+        for i in range(3):
+            s[i, i] = s[i, i] + l[:, None] * tr
+        return s
+
+    def divergence(s):
+        return np.concatenate([sum(div[j] @ s[i, j] for j in range(3)) for i in range(3)])
+
+    K = divergence(stress(strain_from_u(np.eye(3 * N))))
+    Eb = O.voigt_to_tensor(np.asarray(E, float))[:, :, None, None] * np.ones((1, 1, N, 1))
+    rhs = -divergence(stress(Eb))
+    u, *_ = np.linalg.lstsq(K, rhs, rcond=None)
+    eps = Eb + strain_from_u(u)
+    return np.stack([eps[i, j, :, 0] for (i, j) in O.VOIGT])
+
+
+@pytest.mark.parametrize("scheme,grad_kind,div_kind,n", [
+    ("CD", "CD", "CD", 4), ("ACD", "ACD", "ACD", 4), ("AFB_R", "AFD", "ABD", 4), ("AHC", "AFD", "ABD", 4),
+    ("F", "F", "F", 5)])
+def test_fixed_point_equals_dense_real_space_solve(scheme, grad_kind, div_kind, n):
+    """The iterated fixed point equals a direct solve of the real-space stencil equations
+    (Sec. 5.3 stencils; for F the spectral differentiation matrix, odd n), brute force at n^3."""
+    lam, mu = M.random_field(n, n, n, seed=11)
+    E = np.array([0.01, 0.0, -0.003, 0.0, 0.002, 0.004])
+    r = O.solve(lam, mu, scheme, E, tol=1e-13, maxit=5000)
+    assert r.converged
+    if grad_kind == "F":
+        grad = div = _fourier_diff_matrices(n)
+    else:
+        grad = _stencil_matrices(grad_kind, n, n, n)
+        div = _stencil_matrices(div_kind, n, n, n)
+    eps = _dense_equilibrium_strain(lam, mu, E, grad, div)
+    np.testing.assert_allclose(r.eps.reshape(6, -1), eps, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------- DGO
+@pytest.mark.parametrize("power", [1, 2])
+def test_dgo_weights_partition_of_unity(power):
+    """S_m(x) = sum_{nu=-m}^{m-1} sinc^p(pi (nu + x)) -> 1 for p = 1 and p = 2 (alias-sum weights)."""
+    errs = []
+    for m in (4, 16, 64, 256):
+        Sm = sum(O.sinc_weight(np.array([nu * 16 + 6]), 16)[0] ** power for nu in range(-m, m))
+        errs.append(abs(Sm - 1.0))
+    assert errs[-1] < errs[0] and errs[-1] < 2e-3
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_dgo_1d_closed_form(power):
+    """In 1D Gamma_H(k) = -1/C_H for all k, so Gamma^c_omega = -S_m(omega/n)/C_H, Gamma^c_0 = 0."""
+    n = 8
+    lam_h, mu_h = 0.0, 2.0
+    G = O.dgo_operator(1, 1, n, 1.0, lam_h, mu_h, power=power)
+    g11 = G[0, 0, 0, 0, 0, :]
+    om = np.arange(n)
+    Sm = np.array([sum((np.sin(np.pi * (nu + w / n)) / (np.pi * (nu + w / n))) ** power for nu in range(-4, 4))
+                   for w in om[1:]])
+    np.testing.assert_allclose(g11[1:], -Sm / (lam_h + 2 * mu_h), atol=1e-14)
+    assert g11[0] == 0.0
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_dgo_on_axis_closed_form_and_symmetry(power):
+    """Gamma^c(omega1, 0, 0) = Gamma_H(e1) S_m(omega1/n); Gamma^c(n - omega) = Gamma^c(omega), real."""
+    n = 6
+    lam_h, mu_h = 1.3, 0.6
+    G = O.dgo_operator(n, n, n, 1.0, lam_h, mu_h, power=power)
+    e1 = np.array([[1.0], [0.0], [0.0]])
+    Gh = O.green_hat_iso(e1, lam_h, mu_h)[0]
+    for w in range(1, n):
+        Sm = sum((np.sin(np.pi * (nu + w / n)) / (np.pi * (nu + w / n))) ** power for nu in range(-3, 3))
+        for p, (i, j) in enumerate(O.VOIGT):
+            B = np.zeros((3, 3))
+            B[i, j] = B[j, i] = 1.0
+            Bk = B @ e1[:, 0]
+            ref = -0.5 * (np.outer(Gh @ Bk, e1[:, 0]) + np.outer(e1[:, 0], Gh @ Bk)) * Sm
+            np.testing.assert_allclose(G[p][:, :, 0, 0, w], ref, atol=1e-13)
+    idx = (-np.arange(n)) % n
+    np.testing.assert_allclose(G, G[..., idx, :, :][..., :, idx, :][..., :, :, idx], atol=1e-13)
+
+
+def test_dgo_polarization_1d_equals_direct_solve():
+    """1D DGO, polarization form: the fixed point solves E = E_bar + F^+ diag(-S_m / C_H) F^- (C - C_H) E,
+    assembled here with numpy's FFT and the closed-form 1D operator, and solved directly."""
+    n = 10
+    rng = np.random.default_rng(4)
+    C = np.exp(rng.uniform(np.log(0.5), np.log(30.0), n))
+    lam = np.zeros((1, 1, n))
+    mu = (0.5 * C).reshape(1, 1, n)
+    r = O.solve(lam, mu, "DGO", [1.0, 0, 0, 0, 0, 0], tol=1e-14, maxit=5000)
+    assert r.converged
+    C_H = 0.5 * (C.min() + C.max())
+    w = np.arange(n)
+    Sm = np.array([sum((np.sin(np.pi * (nu + x / n)) / (np.pi * (nu + x / n))) ** 2 for nu in range(-5, 5))
+                   if x else 0.0 for x in w])
+    # column j of the operator: E_bar-free part applied to unit vectors
+    Op = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        Op[:, j] = np.fft.ifft(-Sm / C_H * np.fft.fft((C - C_H) * e)).real
+    E = np.linalg.solve(np.eye(n) - Op, np.ones(n))
+    np.testing.assert_allclose(r.eps[0, 0, 0], E, rtol=1e-11)
+
+
+# ----------------------------------------------------------------------------- gradient
+def test_gradient_closed_form_matches_finite_differences():
+    lam, mu = M.random_field(4, 4, 4, seed=7)
+    I, J = 0, 0
+    scheme = "AFB_R"
+    ref = O.default_reference(lam, mu)
+    EI = np.zeros(6); EI[I] = 1.0
+    EJ = np.zeros(6); EJ[J] = 1.0
+    rI = O.solve(lam, mu, scheme, EI, tol=1e-14, maxit=20000, ref=ref)
+    rJ = O.solve(lam, mu, scheme, EJ, tol=1e-14, maxit=20000, ref=ref)
+    gl, gm = O.gradient_closed_form(rI.eps, rJ.eps)
+    vox = [0, 17, 42]
+    fl, fm = O.gradient_fd(lam, mu, scheme, I, J, vox, rel_step=1e-5, tol=1e-14)
+    np.testing.assert_allclose(gl.ravel()[vox], fl, rtol=1e-5)
+    np.testing.assert_allclose(gm.ravel()[vox], fm, rtol=1e-5)
+
+
+def test_paper_increment_stop_rule_runs():
+    lam, mu = M.random_field(4, 4, 4, seed=1)
+    r = O.solve(lam, mu, "AFB_R", [0.01, 0, 0, 0, 0, 0], tol=1e-12, stop_rule=1, maxit=500)
+    assert r.converged and r.iters > 2
