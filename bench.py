@@ -1,0 +1,218 @@
+"""Benchmark of the Green-function-preconditioned fixed-point iteration on one GB300.
+
+A step is one iteration of the hot path (stress, forward 3D transform, Green operator, residual,
+inverse transform, strain update) over the whole cell.  The default workload is a 256^3 cell of
+random non-overlapping voxelised spheres (radius U[6, 16] voxels, volume fraction 0.25, contrast 100,
+seed 0), PCD sampling, AFB/R wave vectors.  The metric is voxel-iterations per second.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iterations/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def workload(n, seed=0):
+    from paper_2009_03762_gb300 import microstructure as M
+    return M.random_spheres(n, vf=0.25, rmin=6.0, rmax=16.0, contrast=100.0, seed=seed)
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0],
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bytes_per_voxel_fp64(n):
+    """Algorithmic HBM bytes per voxel of each pass (FP64): pass_x reads the half spectrum, eps, lambda,
+    mu and writes eps and the half spectrum; the y and z passes read and write the half spectrum."""
+    h = (n // 2 + 1) / n
+    spec = 6 * 16 * h
+    return {"pass_x": 2 * spec + 2 * 48 + 16, "pass_y": 2 * spec, "pass_z_gamma": 2 * spec}
+
+
+def run_gfp(args):
+    import torch
+    from paper_2009_03762_gb300 import gfp
+
+    n = args.n
+    N = n ** 3
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lam, mu = workload(n)
+    stream = torch.cuda.current_stream()
+    g = gfp.Grid(n, n, n, 1.0, stream.cuda_stream)
+    lam_d = torch.from_numpy(lam).to(dev)
+    mu_d = torch.from_numpy(mu).to(dev)
+    g.set_phases(lam_d, mu_d)
+    sch = gfp.scheme(args.op, "PCD", "FP64")
+    E = [0.0, 0.0, 0.0, 0.0, 0.0, 0.5]
+    K, W = args.steps, args.warmup
+    # warm-up
+    g.solve(sch, E, 0.0, W)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = g.solve(sch, E, 0.0, K)      # exactly K iterations (tol = 0), inputs resident in HBM
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    assert r.iters == K
+    value = N * K / (ms * 1e-3)
+    # per-kernel durations on the same stream (dominant kernel for the roofline)
+    pass_ms = g.time_passes(sch, max(3, min(K, 10)))
+    names = ["pass_x", "pass_y", "pass_z_gamma", "reduce_eta", "pass_y_inv"]
+    bpv = bytes_per_voxel_fp64(n)
+    shares = {nm: float(t) for nm, t in zip(names, pass_ms)}
+    dom = max(("pass_x", "pass_y", "pass_z_gamma"), key=lambda k: shares[k])
+    peak, peak_kind = hbm_peak()
+    achieved = bpv[dom] * N / (shares[dom] * 1e-3) / 1e9
+    # end to end through the C ABI with host buffers: H2D of lambda, mu, K iterations, D2H of the strain
+    eps_host = np.empty((6, n, n, n))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.set_phases(lam, mu)
+    r2 = g.solve(sch, E, 0.0, K)
+    g.strain(eps_host)
+    t_e2e = time.perf_counter() - t0
+    e2e = N * K / t_e2e
+    line = {
+        "metric": METRIC, "value": value, "unit": "voxel-iterations/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "random spheres %d^3, vf 0.25, r U[6,16], contrast 100, PCD, %s, FP64" % (n, args.op),
+                   "grid": n, "scheme": args.op, "precision": "FP64", "l2": "inputs larger than L2 (spectrum %.0f MB)"
+                   % (6 * 16 * (n // 2 + 1) * n * n / 1e6)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_voxel": bpv[dom]},
+        "pass_ms": shares,
+        "e2e": {"value": e2e, "unit": "voxel-iterations/s", "h2d_bytes_per_step": 2 * N * 8 / K,
+                "d2h_bytes_per_step": 6 * N * 8 / K},
+        "gpu_launches": 5 * K + 1,
+        "clocks": clk,
+    }
+    g.close()
+    return line
+
+
+def oracle_sample(n, op, iters):
+    """Time the FP64 oracle as it stands on `iters` iterations of the same workload."""
+    from oracle import gfp_oracle as O
+    lam, mu = workload(n)
+    t0 = time.perf_counter()
+    O.solve(lam, mu, op, [0, 0, 0, 0, 0, 0.5], disc="PCD", max_iters_exact=iters)
+    dt = time.perf_counter() - t0
+    return n ** 3 * iters / dt, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfp", choices=["gfp", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--op", default="AFB_R")
+    ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, dt = oracle_sample(args.oracle_n, args.op, 1)
+        steps = []
+        for _ in range(args.steps):
+            steps.append(oracle_sample(args.oracle_n, args.op, 1)[1])
+        dt = float(np.sum(steps))
+        value = args.oracle_n ** 3 * args.steps / dt
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "voxel-iterations/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "random spheres %d^3 sample of the %d^3 workload, %s, FP64 oracle"
+                           % (args.oracle_n, args.n, args.op)},
+                "cpu_baseline": {"value": value, "unit": "voxel-iterations/s", "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": "%d single iterations of a %d^3 cell" % (args.steps, args.oracle_n)},
+                "e2e": {"value": value, "unit": "voxel-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    line = run_gfp(args)
+    if not args.no_cpu_baseline and rank == 0:
+        v, dt = oracle_sample(args.oracle_n, args.op, 1)
+        line["cpu_baseline"] = {"value": v, "unit": "voxel-iterations/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": "1 iteration of the same workload at %d^3 (%.1f s)" % (args.oracle_n, dt)}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,140 @@
+/*
+ * gfp.h -- C ABI of the GB300 Green-function-preconditioned (GFP) fixed-point solver for the
+ * periodic linear-elastic unit-cell problem (Khorrami, Mianroodi, Shanthraj, Svendsen,
+ * "Development and comparison of spectral algorithms for numerical modeling of the
+ * quasi-static mechanical behavior of inhomogeneous materials").
+ *
+ * One iteration (Sec. 5.2 Algorithm T-3D, Sec. 5.4 Algorithms P-3D and D-3D, in strain form):
+ *   sigma = C(x) : eps                       (isotropic C, Sec. 5.1)
+ *   T_check = forward 3D DFT of sigma         (eq. DisFouMat3D)
+ *   eta = ||T_check q^b|| / ||T_check(0)||_F  (equilibrium residual; stop when eta < tol)
+ *   Delta E_check = -Gamma(k) T_check         (Gamma from eq. EquMecFunGre3D, or Gamma^c of Alg. D)
+ *   eps += inverse 3D DFT of Delta E_check    (the mean strain stays the prescribed E_bar)
+ *
+ * Conventions
+ *   - Grids are n1 x n2 x n3 voxels, spacing h; every n_r must factor as 2^a 3^b, n_r <= 1024.
+ *   - Fields are structure-of-arrays in C order with x1 fastest: field[c][i3][i2][i1].
+ *   - Symmetric tensors use the six tensor components (11, 22, 33, 23, 13, 12) with no factor 2;
+ *     only C_eff uses the Voigt (engineering shear) convention: for load J the mean strain is the
+ *     Voigt unit vector e_J (tensor shear 1/2) and column J of C_eff is the mean stress.
+ *   - "where" = 0 means a host pointer, 1 a device pointer (read or written in stream order on the
+ *     grid's stream).  Output buffers are owned by the caller; the grid owns every device
+ *     allocation it makes.  No pointer is kept beyond the call.
+ *   - Every call returns a gfp_status.  Nothing is thrown across the ABI.  Calls on one grid are
+ *     not thread-safe; distinct grids are independent.
+ */
+#ifndef GFP_H
+#define GFP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfp_grid_s* gfp_grid;
+
+typedef enum {
+  GFP_OK = 0,
+  GFP_ERR_ARG = -1,              /* bad argument (null pointer, negative size, NaN/non-positive mu, ...) */
+  GFP_ERR_UNSUPPORTED_SIZE = -2, /* a grid size is not 2^a 3^b or exceeds the limit */
+  GFP_ERR_OOM = -3,              /* device allocation failed */
+  GFP_ERR_NOT_CONVERGED = -4,    /* maxit reached; the result is still filled */
+  GFP_ERR_DIVERGED = -5,         /* eta is NaN/Inf or grew over a long window */
+  GFP_ERR_DEVICE_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+  GFP_ERR_CUDA = -7,             /* a CUDA runtime call failed */
+  GFP_ERR_UNSUPPORTED = -8       /* combination not implemented (e.g. mixed precision with DGO) */
+} gfp_status;
+
+/* Discretization of Sec. 3 (TD: trapezoidal, material sampled at x_i = (i-1)h; PCD: piecewise
+ * constant, sampled at x_i^c = (i-1/2)h).  For the finite-difference schemes the half-cell phases of
+ * the PCD transforms cancel (Sec. 3.2, "independent of s"), so both run the same iteration on the
+ * given samples; the field tells which sampling the caller used.  DGO is PCD by definition. */
+typedef enum { GFP_TD = 0, GFP_PCD = 1 } gfp_disc;
+
+/* Effective wave vectors (Sec. 5.3, eqs. FreDifFinFBDF3D, FreDifFinFBDFR3D, EffNumWavConWil3D):
+ *   GFP_F     plain Fourier q = i k, conjugate pairing
+ *   GFP_CD    central differences, conjugate pairing
+ *   GFP_ACD   averaged central differences, conjugate pairing
+ *   GFP_HC    half-central differences, conjugate pairing
+ *   GFP_AHC   averaged half-central differences, conjugate pairing
+ *   GFP_AFB_R (AFD, AhC) average forward-backward / Willot's rotated scheme R
+ *   GFP_DGO   discrete Green operator of Algorithm D-3D (alias sum over nu in [-m, m-1]^3)
+ * For every pairing except DGO, q^a = e^{i phi} i kt and q^b = +-e^{-i phi'} i kt with one real vector
+ * kt(k), and the strain increment is -Gamma0_iso(lambda_H, mu_H; kt) T_check, so AHC and AFB_R give
+ * identical iterates. */
+typedef enum { GFP_F = 0, GFP_CD = 1, GFP_ACD = 2, GFP_HC = 3, GFP_AHC = 4, GFP_AFB_R = 5, GFP_DGO = 6 } gfp_op;
+
+typedef enum { GFP_FP64 = 0, GFP_MIXED = 1 } gfp_prec;
+
+typedef struct {
+  int disc;       /* gfp_disc */
+  int op;         /* gfp_op */
+  int dgo_m;      /* DGO alias half-range m (<= 0: n_r / 2 per axis, at least 1) */
+  int prec;       /* gfp_prec: FP64 throughout, or FP32 FFT/Gamma/stress inner iterations inside an
+                     FP64 outer loop (FP64 residual, mean strain and refinement correction) */
+  int stop_rule;  /* 0: equilibrium residual eta (default); DGO uses the strain increment norm */
+} gfp_scheme;
+
+typedef struct {
+  int iters;              /* iterations (stress evaluations); a homogeneous cell reports 1 */
+  int outer;              /* mixed precision: FP64 outer passes (0 in FP64 mode) */
+  double residual;        /* final eta */
+  double sigma_mean[6];   /* mean stress, tensor components (11,22,33,23,13,12) */
+  int status;             /* gfp_status of the solve */
+  double* residual_history; /* caller-owned host array of history_cap doubles, or NULL */
+  int history_cap;
+} gfp_result;
+
+/* Create a grid of n1 x n2 x n3 voxels with spacing h on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream).  Allocates every device buffer the solver needs (about (6*8 + 6*16*(n1/2+1)/n1 + 16)
+ * bytes per voxel in FP64 mode).  On success *out receives the handle. */
+int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_grid* out);
+
+/* Per-voxel Lame fields lambda, mu ([n3][n2][n1] float64; where = 0 host, 1 device).  They are the
+ * samples C_i = C(x_i) (TD) or C(x_i^c) (PCD) of Algorithms T/P/D.  ref_lambda_mu may give the
+ * reference medium (lambda_H, mu_H); NULL selects 1/2 (min + max) of each constant over the grid
+ * (Sec. 4: C_H = 1/2 (C_M + C_I)).  mu must be > 0 and finite, lambda finite. */
+int gfp_set_phases(gfp_grid g, const double* lambda, const double* mu, int where, const double* ref_lambda_mu);
+
+/* Solve for the strain with prescribed mean E_macro (6 tensor components) until eta < tol or
+ * maxit iterations.  The result's fields are filled even when the status is NOT_CONVERGED. */
+int gfp_solve(gfp_grid g, const gfp_scheme* scheme, const double E_macro[6], double tol, int maxit,
+              gfp_result* out);
+
+/* Copy the current strain field (6 x [n3][n2][n1] float64, tensor components) to dst. */
+int gfp_get_strain(gfp_grid g, double* dst, int where);
+
+/* Effective stiffness: six solves with the Voigt unit loads; C_eff is 6x6 row-major (Voigt),
+ * iters[6] receives the iteration count of each load (may be NULL). */
+int gfp_effective_stiffness(gfp_grid g, const gfp_scheme* scheme, double tol, int maxit, double C_eff[36],
+                            int iters[6]);
+
+/* Sensitivities of C_eff,IJ (0 <= I, J < 6) to the per-voxel Lame constants:
+ * dC_dlambda[i] = (1/N) tr eps^I_i tr eps^J_i,  dC_dmu[i] = (2/N) eps^I_i : eps^J_i,
+ * where eps^I is the converged forward field of load I and eps^J the adjoint field, which for the
+ * symmetric Gamma of every scheme here is the forward field of load J.  Outputs [n3][n2][n1]
+ * float64 (where = 0 host, 1 device). */
+int gfp_grad(gfp_grid g, const gfp_scheme* scheme, int I, int J, double tol, int maxit, double* dC_dlambda,
+             double* dC_dmu, int where);
+
+/* Checkpoint/resume: the strain field and the iteration count fully determine a solve's state. */
+int gfp_get_state(gfp_grid g, double* eps_dst, int* iters);
+int gfp_set_state(gfp_grid g, const double* eps_src, int iters);
+
+/* Measurement hook: runs `iters` iterations of the hot path on the grid's current strain (the
+ * convergence test is disabled) with CUDA events around each kernel on the grid's stream, and returns
+ * the mean duration in milliseconds of pass_x, pass_y (forward), pass_z_gamma, the residual reduction
+ * and pass_y (inverse) in pass_ms[0..4].  The strain is modified as by `iters` iterations. */
+int gfp_time_passes(gfp_grid g, const gfp_scheme* scheme, int iters, double pass_ms[5]);
+
+int gfp_destroy_grid(gfp_grid g);
+
+/* Static message for a status code. */
+const char* gfp_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFP_H */

@@ -1,0 +1,607 @@
+// C ABI of the GFP solver: grid handles, phases, the iteration driver, effective stiffness,
+// sensitivities and checkpoint/resume.  See include/gfp.h for the contract of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/gfp.h"
+#include "gfp_kernels.cuh"
+
+using namespace gfp;
+
+// ------------------------------------------------------------------------------- small kernels
+namespace gfp {
+
+__global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, SolveState* st, double* hist,
+                                  int hist_cap) {
+  if (st->done) return;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double* t = st->T0;
+    const double t0 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + 2.0 * (t[3] * t[3] + t[4] * t[4] + t[5] * t[5]);
+    const double sum = sh[0];
+    double eta;
+    if (t0 > 0.0) eta = sqrt(sum / t0);
+    else eta = (sum > 0.0) ? INFINITY : 0.0;
+    const int it = st->it + 1;
+    st->it = it;
+    const double prev = st->eta;
+    st->eta = eta;
+    if (hist && it - 1 < hist_cap) hist[it - 1] = eta;
+    if (!(eta == eta) || isinf(eta)) {
+      st->done = 3;
+    } else if (eta < st->tol) {
+      st->done = 1;
+    } else {
+      if (it > 1 && eta > prev) st->growth += 1; else st->growth = 0;
+      if (eta < st->eta_min) st->eta_min = eta;
+      if (st->growth >= 50) st->done = 3;
+      else if (it >= st->maxit) st->done = 2;
+    }
+  }
+}
+
+void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap) {
+  reduce_eta_kernel<<<1, 256, 0, s>>>(partials, np, st, hist, hist_cap);
+}
+
+__global__ void fill_eps_kernel(double* eps, long long N, double e0, double e1, double e2, double e3, double e4,
+                                double e5) {
+  const double e[6] = {e0, e1, e2, e3, e4, e5};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) eps[c * N + i] = e[c];
+  }
+}
+
+// min/max of lambda and mu and a count of invalid entries (mu <= 0 or non-finite values)
+__global__ void phase_stats_kernel(const double* lam, const double* mu, long long N, double* out_minmax,
+                                   unsigned long long* bad) {
+  __shared__ double s[4][256];
+  double lmin = INFINITY, lmax = -INFINITY, mmin = INFINITY, mmax = -INFINITY;
+  unsigned long long nb = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double l = lam[i], m = mu[i];
+    if (!isfinite(l) || !isfinite(m) || !(m > 0.0)) { nb++; continue; }
+    lmin = fmin(lmin, l); lmax = fmax(lmax, l); mmin = fmin(mmin, m); mmax = fmax(mmax, m);
+  }
+  s[0][threadIdx.x] = lmin; s[1][threadIdx.x] = -lmax; s[2][threadIdx.x] = mmin; s[3][threadIdx.x] = -mmax;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = fmin(s[q][threadIdx.x], s[q][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (nb) atomicAdd(bad, nb);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) out_minmax[blockIdx.x * 4 + q] = s[q][0];
+  }
+}
+
+// dC_IJ/dlambda_i = (1/N) tr eI tr eJ, dC_IJ/dmu_i = (2/N) eI : eJ (symmetric tensors, 6 comps)
+__global__ void grad_contract_kernel(const double* eI, const double* eJ, long long N, double* dl, double* dm) {
+  const double invN = 1.0 / (double)N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double a[6], b[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { a[c] = eI[c * N + i]; b[c] = eJ[c * N + i]; }
+    const double trI = a[0] + a[1] + a[2], trJ = b[0] + b[1] + b[2];
+    const double dd = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + 2.0 * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
+    dl[i] = trI * trJ * invN;
+    dm[i] = 2.0 * dd * invN;
+  }
+}
+
+}  // namespace gfp
+
+// ------------------------------------------------------------------------------- the grid
+struct gfp_grid_s {
+  int n1, n2, n3;
+  double h;
+  cudaStream_t stream;
+  Dims d;
+  FftPlan plan[3];
+  LaunchCfg lc64;
+  double* lam = nullptr;
+  double* mu = nullptr;
+  double lam_h = 0, mu_h = 0;
+  bool phases = false;
+  double* eps = nullptr;
+  double2* spec = nullptr;
+  double2* tw64[3] = {nullptr, nullptr, nullptr};
+  double* tabA[3] = {nullptr, nullptr, nullptr};
+  double* tabB[3] = {nullptr, nullptr, nullptr};
+  int table_op = -1;
+  double* partials = nullptr;
+  int np_max = 0;
+  SolveState* st = nullptr;
+  SolveState* st_host = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double* scratch = nullptr;  // small device scratch (min/max partials)
+  unsigned long long* bad = nullptr;
+  double* eps_save = nullptr; // second strain field for gradients
+  int state_iters = 0;
+  bool resume_pending = false; // gfp_set_state was called: the next solve continues from it
+};
+
+namespace {
+
+const int kMaxN = 1024;
+
+bool factor_ok(int n) {
+  if (n < 1 || n > kMaxN) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+FftPlan make_plan(int n) {
+  FftPlan p;
+  p.n = n;
+  p.nst = 0;
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  int n16 = a / 4, r = a % 4;
+  std::vector<int> rad;
+  if (r == 1 && n16 > 0) { n16 -= 1; rad.push_back(8); rad.push_back(4); }
+  else if (r == 1) rad.push_back(2);
+  else if (r == 2) rad.push_back(4);
+  else if (r == 3) rad.push_back(8);
+  for (int i = 0; i < n16; ++i) rad.insert(rad.begin(), 16);
+  for (int i = 0; i < b; ++i) rad.push_back(3);
+  for (size_t i = 0; i < rad.size(); ++i) p.radix[p.nst++] = rad[i];
+  return p;
+}
+
+int round32(int x) { return ((x + 31) / 32) * 32; }
+
+// Tile shapes per pass, bounded by the shared memory of one CTA (two ping-pong tile copies plus
+// the twiddles) and by 32-byte row segments in the strided y/z passes.
+LaunchCfg make_cfg(const Dims& d, int eb) {
+  const long long budget = 200 * 1024;
+  auto clampt = [](int t) { return std::min(512, std::max(64, round32(t))); };
+  LaunchCfg c;
+  int L = std::max(1, std::min(16, 2048 / d.n1));
+  L = (int)std::min<long long>(L, (long long)d.n2 * d.n3);
+  while (L > 1 && (long long)(d.n1 + 6 * L * d.n1) * eb > budget) L /= 2;
+  c.x_lines = L;
+  c.x_threads = clampt(3 * L * d.n1 / 8);
+  int yc = eb == 16 ? 8 : 16;
+  while (yc > 1 && (long long)(d.n2 + 2 * yc * d.n2) * eb > budget) yc /= 2;
+  c.y_cols = std::max(1, std::min(yc, d.n1h));
+  c.y_threads = clampt(c.y_cols * d.n2 / 8);
+  int zc = 4;
+  while (zc > 1 && (long long)(d.n3 + 12 * zc * d.n3) * eb > budget) zc /= 2;
+  c.z_cols = std::max(1, std::min(zc, d.n1h));
+  c.z_threads = clampt(6 * c.z_cols * d.n3 / 8);
+  c.z_blocks = ((d.n1h + c.z_cols - 1) / c.z_cols) * d.n2;
+  return c;
+}
+
+// Per-axis tables with exact zeros (kappa from the storage index; Nyquist is kappa = -n/2)
+void build_tables(int op, int n, double h, std::vector<double>& A, std::vector<double>& B) {
+  A.assign(n, 0.0);
+  B.assign(n, 1.0);
+  const double pi = 3.14159265358979323846;
+  auto md = [](long long a, long long m) { long long r = a % m; return r < 0 ? r + m : r; };
+  for (int i = 0; i < n; ++i) {
+    const long long kap = (i < (n + 1) / 2) ? i : i - n;
+    const double th = 2.0 * pi * (double)kap / (double)n;
+    switch (op) {
+      case OP_F: A[i] = th / h; break;
+      case OP_CD: A[i] = md(2 * kap, n) == 0 ? 0.0 : std::sin(th) / h; break;
+      case OP_ACD:
+        A[i] = md(2 * kap, n) == 0 ? 0.0 : std::sin(th) / h;
+        B[i] = md(4 * kap - n, 2LL * n) == 0 ? 0.0 : std::cos(th);
+        break;
+      case OP_HC: A[i] = md(kap, n) == 0 ? 0.0 : 2.0 * std::sin(0.5 * th) / h; break;
+      case OP_AHC:
+      case OP_AFB_R:
+      default:
+        A[i] = md(kap, n) == 0 ? 0.0 : 2.0 * std::sin(0.5 * th) / h;
+        B[i] = md(2 * kap - n, 2LL * n) == 0 ? 0.0 : std::cos(0.5 * th);
+        break;
+    }
+  }
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? GFP_OK : (e == cudaErrorMemoryAllocation ? GFP_ERR_OOM : GFP_ERR_CUDA); }
+
+#define GFP_CU(call)                         \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+std::once_flag g_setup_once;
+cudaError_t g_setup_err = cudaSuccess;
+
+int global_setup() {
+  std::call_once(g_setup_once, [] {
+    g_setup_err = Passes<double>::setup();
+    if (g_setup_err == cudaSuccess) g_setup_err = Passes<float>::setup();
+  });
+  return cuda_status(g_setup_err);
+}
+
+void free_grid(gfp_grid g) {
+  if (!g) return;
+  cudaFree(g->lam); cudaFree(g->mu); cudaFree(g->eps); cudaFree(g->spec);
+  for (int r = 0; r < 3; ++r) { cudaFree(g->tw64[r]); cudaFree(g->tabA[r]); cudaFree(g->tabB[r]); }
+  cudaFree(g->partials); cudaFree(g->st); cudaFree(g->hist); cudaFree(g->scratch); cudaFree(g->bad);
+  cudaFree(g->eps_save);
+  if (g->st_host) cudaFreeHost(g->st_host);
+  delete g;
+}
+
+int ensure_tables(gfp_grid g, int op) {
+  if (g->table_op == op) return GFP_OK;
+  const int ns[3] = {g->n1, g->n2, g->n3};
+  for (int r = 0; r < 3; ++r) {
+    std::vector<double> A, B;
+    build_tables(op, ns[r], g->h, A, B);
+    GFP_CU(cudaMemcpyAsync(g->tabA[r], A.data(), sizeof(double) * ns[r], cudaMemcpyHostToDevice, g->stream));
+    GFP_CU(cudaMemcpyAsync(g->tabB[r], B.data(), sizeof(double) * ns[r], cudaMemcpyHostToDevice, g->stream));
+  }
+  GFP_CU(cudaStreamSynchronize(g->stream));
+  g->table_op = op;
+  return GFP_OK;
+}
+
+int ensure_hist(gfp_grid g, int cap) {
+  if (cap <= g->hist_cap) return GFP_OK;
+  cudaFree(g->hist);
+  g->hist = nullptr;
+  g->hist_cap = 0;
+  GFP_CU(cudaMalloc(&g->hist, sizeof(double) * cap));
+  g->hist_cap = cap;
+  return GFP_OK;
+}
+
+void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta) {
+  const Dims& d = g->d;
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, have_delta, g->st);
+  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st);
+  launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, g->hist, g->hist_cap);
+  Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+}
+
+// resume: continue from the strain set by gfp_set_state; its iteration count K is taken as the
+// count before the stress evaluation of that strain, so a resumed solve re-evaluates iteration K
+// and then follows exactly the iterates (and counts) of an uninterrupted solve.
+int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, int maxit, gfp_result* out,
+               bool resume) {
+  int rc = ensure_tables(g, sc->op);
+  if (rc) return rc;
+  rc = ensure_hist(g, std::max(maxit, 1));
+  if (rc) return rc;
+  GammaParams<double> gp;
+  for (int r = 0; r < 3; ++r) { gp.A[r] = g->tabA[r]; gp.B[r] = g->tabB[r]; }
+  gp.c_mu = 1.0 / (2.0 * g->mu_h);
+  gp.c_lm = (g->lam_h + g->mu_h) / (g->mu_h * (g->lam_h + 2.0 * g->mu_h));
+  gp.invN = 1.0 / (double)g->d.N;
+  gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
+  SolveState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.maxit = maxit;
+  s0.tol = tol;
+  s0.eta = INFINITY;
+  s0.eta_min = INFINITY;
+  const int start_it = resume ? std::max(0, g->state_iters - 1) : 0;
+  s0.it = start_it;
+  if (start_it >= maxit) return GFP_ERR_ARG;
+  if (!resume) {
+    fill_eps_kernel<<<std::min<long long>(4096, (g->d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, g->d.N, E[0], E[1],
+                                                                                            E[2], E[3], E[4], E[5]);
+  }
+  *g->st_host = s0;
+  GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+  int launched = 0;
+  int chunk = 2;
+  const int budget = maxit - start_it;
+  while (launched < budget) {
+    const int nb = std::min(chunk, budget - launched);
+    for (int b = 0; b < nb; ++b) one_iteration64(g, gp, (launched + b) > 0 ? 1 : 0);
+    launched += nb;
+    GFP_CU(cudaGetLastError());
+    GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
+    GFP_CU(cudaStreamSynchronize(g->stream));
+    if (g->st_host->done) break;
+    chunk = std::min(chunk * 2, 64);
+  }
+  const SolveState& s = *g->st_host;
+  g->state_iters = s.it;
+  int status = GFP_OK;
+  if (s.done == 2 || s.done == 0) status = GFP_ERR_NOT_CONVERGED;
+  if (s.done == 3) status = GFP_ERR_DIVERGED;
+  if (out) {
+    out->iters = s.it;
+    out->outer = 0;
+    out->residual = s.eta;
+    for (int c = 0; c < 6; ++c) out->sigma_mean[c] = s.T0[c] / (double)g->d.N;
+    out->status = status;
+    if (out->residual_history && out->history_cap > 0) {
+      const int nh = std::min(out->history_cap, std::min(s.it, g->hist_cap));
+      if (nh > 0)
+        GFP_CU(cudaMemcpy(out->residual_history, g->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    }
+  }
+  return status;
+}
+
+bool scheme_ok(const gfp_scheme* sc) {
+  return sc && sc->op >= 0 && sc->op <= OP_DGO && (sc->disc == GFP_TD || sc->disc == GFP_PCD) &&
+         (sc->prec == GFP_FP64 || sc->prec == GFP_MIXED);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* gfp_error_string(int status) {
+  switch (status) {
+    case GFP_OK: return "ok";
+    case GFP_ERR_ARG: return "bad argument";
+    case GFP_ERR_UNSUPPORTED_SIZE: return "unsupported grid size (each n must be 2^a 3^b and <= 1024)";
+    case GFP_ERR_OOM: return "device out of memory";
+    case GFP_ERR_NOT_CONVERGED: return "not converged within maxit iterations";
+    case GFP_ERR_DIVERGED: return "iteration diverged";
+    case GFP_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case GFP_ERR_CUDA: return "CUDA runtime error";
+    case GFP_ERR_UNSUPPORTED: return "unsupported scheme/precision combination";
+    default: return "unknown status";
+  }
+}
+
+int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_grid* out) {
+  if (!out) return GFP_ERR_ARG;
+  *out = nullptr;
+  if (!(h > 0.0) || !std::isfinite(h)) return GFP_ERR_ARG;
+  if (n1 < 1 || n2 < 1 || n3 < 1) return GFP_ERR_ARG;
+  if (!factor_ok(n1) || !factor_ok(n2) || !factor_ok(n3)) return GFP_ERR_UNSUPPORTED_SIZE;
+  int rc = global_setup();
+  if (rc) return rc;
+  gfp_grid g = new (std::nothrow) gfp_grid_s();
+  if (!g) return GFP_ERR_OOM;
+  g->n1 = n1; g->n2 = n2; g->n3 = n3; g->h = h;
+  g->stream = (cudaStream_t)cuda_stream;
+  Dims& d = g->d;
+  d.n1 = n1; d.n2 = n2; d.n3 = n3;
+  d.n1h = n1 / 2 + 1;
+  d.P = ((d.n1h + 3) / 4) * 4;
+  d.N = (long long)n1 * n2 * n3;
+  d.S = (long long)n3 * n2 * d.P;
+  const int ns[3] = {n1, n2, n3};
+  for (int r = 0; r < 3; ++r) g->plan[r] = make_plan(ns[r]);
+  g->lc64 = make_cfg(d, 16);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  A((void**)&g->lam, sizeof(double) * d.N);
+  A((void**)&g->mu, sizeof(double) * d.N);
+  A((void**)&g->eps, sizeof(double) * 6 * d.N);
+  A((void**)&g->spec, sizeof(double2) * 6 * d.S);
+  for (int r = 0; r < 3; ++r) {
+    A((void**)&g->tw64[r], sizeof(double2) * ns[r]);
+    A((void**)&g->tabA[r], sizeof(double) * ns[r]);
+    A((void**)&g->tabB[r], sizeof(double) * ns[r]);
+  }
+  g->np_max = g->lc64.z_blocks;
+  A((void**)&g->partials, sizeof(double) * g->np_max);
+  A((void**)&g->st, sizeof(SolveState));
+  A((void**)&g->scratch, sizeof(double) * 4 * 1024);
+  A((void**)&g->bad, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&g->st_host, sizeof(SolveState));
+  if (e != cudaSuccess) { free_grid(g); return cuda_status(e); }
+  // twiddles w_n^j = e^{-2 pi i j / n}
+  const double pi = 3.14159265358979323846;
+  for (int r = 0; r < 3; ++r) {
+    std::vector<double2> tw(ns[r]);
+    for (int j = 0; j < ns[r]; ++j) {
+      const double a = -2.0 * pi * (double)j / (double)ns[r];
+      tw[j].x = std::cos(a);
+      tw[j].y = std::sin(a);
+    }
+    e = cudaMemcpy(g->tw64[r], tw.data(), sizeof(double2) * ns[r], cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_grid(g); return cuda_status(e); }
+  }
+  e = cudaMemsetAsync(g->spec, 0, sizeof(double2) * 6 * d.S, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) { free_grid(g); return cuda_status(e); }
+  *out = g;
+  return GFP_OK;
+}
+
+int gfp_destroy_grid(gfp_grid g) {
+  if (!g) return GFP_ERR_ARG;
+  cudaStreamSynchronize(g->stream);
+  free_grid(g);
+  return GFP_OK;
+}
+
+int gfp_set_phases(gfp_grid g, const double* lambda, const double* mu, int where, const double* ref) {
+  if (!g || !lambda || !mu || (where != 0 && where != 1)) return GFP_ERR_ARG;
+  const long long N = g->d.N;
+  const cudaMemcpyKind k = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  GFP_CU(cudaMemcpyAsync(g->lam, lambda, sizeof(double) * N, k, g->stream));
+  GFP_CU(cudaMemcpyAsync(g->mu, mu, sizeof(double) * N, k, g->stream));
+  const int blocks = (int)std::min<long long>(1024, (N + 255) / 256);
+  GFP_CU(cudaMemsetAsync(g->bad, 0, sizeof(unsigned long long), g->stream));
+  phase_stats_kernel<<<blocks, 256, 0, g->stream>>>(g->lam, g->mu, N, g->scratch, g->bad);
+  GFP_CU(cudaGetLastError());
+  std::vector<double> mm(4 * blocks);
+  unsigned long long bad = 0;
+  GFP_CU(cudaMemcpyAsync(mm.data(), g->scratch, sizeof(double) * 4 * blocks, cudaMemcpyDeviceToHost, g->stream));
+  GFP_CU(cudaMemcpyAsync(&bad, g->bad, sizeof(bad), cudaMemcpyDeviceToHost, g->stream));
+  GFP_CU(cudaStreamSynchronize(g->stream));
+  if (bad) return GFP_ERR_ARG;
+  double q[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+  for (int b = 0; b < blocks; ++b)
+    for (int j = 0; j < 4; ++j) q[j] = std::min(q[j], mm[4 * b + j]);
+  if (ref) {
+    if (!std::isfinite(ref[0]) || !std::isfinite(ref[1]) || !(ref[1] > 0.0) || !(ref[0] + 2.0 * ref[1] > 0.0))
+      return GFP_ERR_ARG;
+    g->lam_h = ref[0];
+    g->mu_h = ref[1];
+  } else {
+    g->lam_h = 0.5 * (q[0] + (-q[1]));
+    g->mu_h = 0.5 * (q[2] + (-q[3]));
+  }
+  g->phases = true;
+  return GFP_OK;
+}
+
+int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, int maxit, gfp_result* out) {
+  if (!g || !scheme_ok(sc) || !E || !(tol >= 0.0) || maxit < 1) return GFP_ERR_ARG;
+  for (int c = 0; c < 6; ++c) if (!std::isfinite(E[c])) return GFP_ERR_ARG;
+  if (!g->phases) return GFP_ERR_ARG;
+  if (sc->op == OP_DGO || sc->prec != GFP_FP64 || sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
+  const bool resume = g->resume_pending;
+  g->resume_pending = false;
+  return solve_fp64(g, sc, E, tol, maxit, out, resume);
+}
+
+int gfp_get_strain(gfp_grid g, double* dst, int where) {
+  if (!g || !dst || (where != 0 && where != 1)) return GFP_ERR_ARG;
+  GFP_CU(cudaMemcpyAsync(dst, g->eps, sizeof(double) * 6 * g->d.N,
+                         where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream));
+  GFP_CU(cudaStreamSynchronize(g->stream));
+  return GFP_OK;
+}
+
+int gfp_effective_stiffness(gfp_grid g, const gfp_scheme* sc, double tol, int maxit, double C_eff[36], int iters[6]) {
+  if (!g || !scheme_ok(sc) || !C_eff || maxit < 1) return GFP_ERR_ARG;
+  int worst = GFP_OK;
+  for (int J = 0; J < 6; ++J) {
+    double E[6] = {0, 0, 0, 0, 0, 0};
+    E[J] = J < 3 ? 1.0 : 0.5;
+    gfp_result r;
+    std::memset(&r, 0, sizeof(r));
+    const int rc = gfp_solve(g, sc, E, tol, maxit, &r);
+    if (rc != GFP_OK && rc != GFP_ERR_NOT_CONVERGED) return rc;
+    if (rc != GFP_OK) worst = rc;
+    for (int I = 0; I < 6; ++I) C_eff[I * 6 + J] = r.sigma_mean[I];
+    if (iters) iters[J] = r.iters;
+  }
+  return worst;
+}
+
+int gfp_grad(gfp_grid g, const gfp_scheme* sc, int I, int J, double tol, int maxit, double* dl, double* dm, int where) {
+  if (!g || !scheme_ok(sc) || I < 0 || I > 5 || J < 0 || J > 5 || !dl || !dm || (where != 0 && where != 1))
+    return GFP_ERR_ARG;
+  const long long N = g->d.N;
+  if (!g->eps_save) GFP_CU(cudaMalloc(&g->eps_save, sizeof(double) * 6 * N));
+  double E[6] = {0, 0, 0, 0, 0, 0};
+  E[I] = I < 3 ? 1.0 : 0.5;
+  gfp_result r;
+  std::memset(&r, 0, sizeof(r));
+  int rc = gfp_solve(g, sc, E, tol, maxit, &r);
+  if (rc != GFP_OK) return rc;
+  GFP_CU(cudaMemcpyAsync(g->eps_save, g->eps, sizeof(double) * 6 * N, cudaMemcpyDeviceToDevice, g->stream));
+  // adjoint field: the transposed Gamma-iteration equals the forward one (Gamma real and symmetric),
+  // so the adjoint state for C_eff,IJ is the forward solution of load J
+  double EJ[6] = {0, 0, 0, 0, 0, 0};
+  EJ[J] = J < 3 ? 1.0 : 0.5;
+  rc = gfp_solve(g, sc, EJ, tol, maxit, &r);
+  if (rc != GFP_OK) return rc;
+  double *odl = dl, *odm = dm;
+  double* tmp = nullptr;
+  if (where == 0) {
+    GFP_CU(cudaMalloc(&tmp, sizeof(double) * 2 * N));
+    odl = tmp;
+    odm = tmp + N;
+  }
+  grad_contract_kernel<<<(int)std::min<long long>(4096, (N + 255) / 256), 256, 0, g->stream>>>(g->eps_save, g->eps, N,
+                                                                                             odl, odm);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && where == 0) {
+    e = cudaMemcpyAsync(dl, odl, sizeof(double) * N, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dm, odm, sizeof(double) * N, cudaMemcpyDeviceToHost, g->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (tmp) cudaFree(tmp);
+  return cuda_status(e);
+}
+
+int gfp_get_state(gfp_grid g, double* eps_dst, int* iters) {
+  if (!g || !eps_dst) return GFP_ERR_ARG;
+  int rc = gfp_get_strain(g, eps_dst, 0);
+  if (rc) return rc;
+  if (iters) *iters = g->state_iters;
+  return GFP_OK;
+}
+
+int gfp_set_state(gfp_grid g, const double* eps_src, int iters) {
+  if (!g || !eps_src || iters < 0) return GFP_ERR_ARG;
+  GFP_CU(cudaMemcpyAsync(g->eps, eps_src, sizeof(double) * 6 * g->d.N, cudaMemcpyHostToDevice, g->stream));
+  GFP_CU(cudaStreamSynchronize(g->stream));
+  g->state_iters = iters;
+  g->resume_pending = true;
+  return GFP_OK;
+}
+
+int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[5]) {
+  if (!g || !scheme_ok(sc) || iters < 1 || !pass_ms || !g->phases) return GFP_ERR_ARG;
+  if (sc->op == OP_DGO || sc->prec != GFP_FP64) return GFP_ERR_UNSUPPORTED;
+  int rc = ensure_tables(g, sc->op);
+  if (rc) return rc;
+  GammaParams<double> gp;
+  for (int r = 0; r < 3; ++r) { gp.A[r] = g->tabA[r]; gp.B[r] = g->tabB[r]; }
+  gp.c_mu = 1.0 / (2.0 * g->mu_h);
+  gp.c_lm = (g->lam_h + g->mu_h) / (g->mu_h * (g->lam_h + 2.0 * g->mu_h));
+  gp.invN = 1.0 / (double)g->d.N;
+  gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
+  SolveState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.maxit = iters + 1;
+  s0.tol = -1.0;  // never converges: every pass runs
+  s0.eta = INFINITY;
+  s0.eta_min = INFINITY;
+  *g->st_host = s0;
+  GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+  const Dims& d = g->d;
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) GFP_CU(cudaEventCreate(&ev[i]));
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int it = 0; it < iters; ++it) {
+    GFP_CU(cudaEventRecord(ev[0], g->stream));
+    Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 1, g->st);
+    GFP_CU(cudaEventRecord(ev[1], g->stream));
+    Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    GFP_CU(cudaEventRecord(ev[2], g->stream));
+    Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st);
+    GFP_CU(cudaEventRecord(ev[3], g->stream));
+    launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
+    GFP_CU(cudaEventRecord(ev[4], g->stream));
+    Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    GFP_CU(cudaEventRecord(ev[5], g->stream));
+    GFP_CU(cudaEventSynchronize(ev[5]));
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  for (int k = 0; k < 5; ++k) pass_ms[k] = acc[k] / iters;
+  return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

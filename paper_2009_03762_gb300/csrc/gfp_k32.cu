@@ -1,0 +1,5 @@
+// FP32 instantiation of the hot-path passes (bulk of the mixed-precision iteration).
+#include "gfp_kimpl.cuh"
+namespace gfp {
+template struct Passes<float>;
+}

@@ -1,0 +1,333 @@
+// Hot-path kernels of one fixed-point iteration (Sec. 5.2 Algorithm T-3D in strain form):
+//
+//   pass_x      : inverse x-transform of the previous increment -> eps += d_eps ->
+//                 sigma = lambda tr(eps) I + 2 mu eps (Sec. 5.1) -> forward real-to-complex x-transform
+//   pass_y      : complex transform along x2 (forward, or inverse)
+//   pass_z_gamma: forward transform along x3 -> residual partial |T kt|^2 and T(0) ->
+//                 Delta E = -Gamma0(kt) T / N (eq. EquMecFunGre3D in its real isotropic form) ->
+//                 inverse transform along x3
+//   reduce_eta  : eta = ||T q^b|| / ||T(0)||_F and the convergence decision (device flag)
+//
+// Data layout (HBM): real fields [c][i3][i2][i1]; the half spectrum [c][k3][k2][k1] with
+// k1 in [0, n1/2] and a row pitch P >= n1/2 + 1 (rows start on 64-byte boundaries).
+#pragma once
+#include "gfp_fft.cuh"
+
+namespace gfp {
+
+enum { OP_F = 0, OP_CD = 1, OP_ACD = 2, OP_HC = 3, OP_AHC = 4, OP_AFB_R = 5, OP_DGO = 6 };
+
+struct Dims {
+  int n1, n2, n3;
+  int n1h;      // n1/2 + 1
+  int P;        // spectrum row pitch (complex elements)
+  long long N;  // n1 n2 n3
+  long long S;  // spectrum component stride = n3 n2 P
+};
+
+// Device-side solver state; one per solve, reset by the host before the first iteration.
+struct SolveState {
+  int it;          // iterations done
+  int done;        // 0 running, 1 converged, 2 maxit reached, 3 diverged
+  int maxit;
+  int growth;      // consecutive iterations with growing eta
+  double tol;
+  double eta;      // last residual
+  double eta_min;
+  double T0[6];    // last unnormalised T(k = 0), tensor components
+};
+
+// Per-axis wave-vector tables: kt_r = A_r[i_r] B_s[i_s] B_t[i_t] ((s, t) the other two axes),
+// indexed by storage index i_r in 0..n_r-1 (kappa = i_r, or i_r - n_r past the middle; the Nyquist
+// index n_r/2 of an even axis is kappa = -n_r/2 as in the paper's index range).
+template <typename R>
+struct GammaParams {
+  const R* A[3];
+  const R* B[3];
+  R c_mu;              // 1 / (2 mu_H)
+  R c_lm;              // (lambda_H + mu_H) / (mu_H (lambda_H + 2 mu_H))
+  R invN;
+  int nyq_avg;         // average Gamma over the Hermitian partner on Nyquist planes (F, HC)
+};
+
+// Real isotropic Gamma0 applied to a symmetric complex tensor t (6 comps), times -scale:
+// out_ij = -scale [ (k_i v_j + k_j v_i) / (2 mu s) - c_lm k_i k_j (k.v) / s^2 ],  v = t k, s = |k|^2.
+template <typename R, typename T>
+__device__ __forceinline__ void gamma0_apply(const T t[6], R k1, R k2, R k3, R c_mu, R c_lm, R scale, T out[6]) {
+  const R s = k1 * k1 + k2 * k2 + k3 * k3;
+  if (s == (R)0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { out[c].x = 0; out[c].y = 0; }
+    return;
+  }
+  T v1, v2, v3;
+  v1.x = t[0].x * k1 + t[5].x * k2 + t[4].x * k3;  v1.y = t[0].y * k1 + t[5].y * k2 + t[4].y * k3;
+  v2.x = t[5].x * k1 + t[1].x * k2 + t[3].x * k3;  v2.y = t[5].y * k1 + t[1].y * k2 + t[3].y * k3;
+  v3.x = t[4].x * k1 + t[3].x * k2 + t[2].x * k3;  v3.y = t[4].y * k1 + t[3].y * k2 + t[2].y * k3;
+  const R is = (R)1 / s;
+  const R a = c_mu * is * scale;               // scale / (2 mu s)
+  T kv; kv.x = k1 * v1.x + k2 * v2.x + k3 * v3.x; kv.y = k1 * v1.y + k2 * v2.y + k3 * v3.y;
+  const R b = c_lm * is * is * scale;
+  T bkv; bkv.x = b * kv.x; bkv.y = b * kv.y;
+  // out = -(a (k_i v_j + k_j v_i) - k_i k_j bkv)
+  out[0].x = -(a * 2 * k1 * v1.x - k1 * k1 * bkv.x); out[0].y = -(a * 2 * k1 * v1.y - k1 * k1 * bkv.y);
+  out[1].x = -(a * 2 * k2 * v2.x - k2 * k2 * bkv.x); out[1].y = -(a * 2 * k2 * v2.y - k2 * k2 * bkv.y);
+  out[2].x = -(a * 2 * k3 * v3.x - k3 * k3 * bkv.x); out[2].y = -(a * 2 * k3 * v3.y - k3 * k3 * bkv.y);
+  out[3].x = -(a * (k2 * v3.x + k3 * v2.x) - k2 * k3 * bkv.x); out[3].y = -(a * (k2 * v3.y + k3 * v2.y) - k2 * k3 * bkv.y);
+  out[4].x = -(a * (k1 * v3.x + k3 * v1.x) - k1 * k3 * bkv.x); out[4].y = -(a * (k1 * v3.y + k3 * v1.y) - k1 * k3 * bkv.y);
+  out[5].x = -(a * (k1 * v2.x + k2 * v1.x) - k1 * k2 * bkv.x); out[5].y = -(a * (k1 * v2.y + k2 * v1.y) - k1 * k2 * bkv.y);
+}
+
+// |T kt|^2 for a symmetric complex tensor (6 comps) and a real vector
+template <typename R, typename T>
+__device__ __forceinline__ R tk_norm2(const T t[6], R k1, R k2, R k3) {
+  const R v1x = t[0].x * k1 + t[5].x * k2 + t[4].x * k3;
+  const R v1y = t[0].y * k1 + t[5].y * k2 + t[4].y * k3;
+  const R v2x = t[5].x * k1 + t[1].x * k2 + t[3].x * k3;
+  const R v2y = t[5].y * k1 + t[1].y * k2 + t[3].y * k3;
+  const R v3x = t[4].x * k1 + t[3].x * k2 + t[2].x * k3;
+  const R v3y = t[4].y * k1 + t[3].y * k2 + t[2].y * k3;
+  return v1x * v1x + v1y * v1y + v2x * v2x + v2y * v2y + v3x * v3x + v3y * v3y;
+}
+
+// --------------------------------------------------------------------------------------------
+// pass_x: one CTA handles `lines` consecutive x1-lines (fixed i3, consecutive i2).
+// --------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict__ eps, const R* __restrict__ lam,
+                              const R* __restrict__ mu, const typename C<R>::T* __restrict__ tw, FftPlan plan, Dims d,
+                              int lines, int have_delta, const SolveState* __restrict__ st) {
+  typedef typename C<R>::T T;
+  if (st->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* bufa = twl + d.n1;                      // [3 pairs][lines][n1], two ping-pong copies
+  T* bufb = bufa + 3 * lines * d.n1;
+  T* buf = bufa;
+  const int n1 = d.n1, n1h = d.n1h;
+  const long long nlines = (long long)d.n2 * d.n3;
+  const long long line0 = (long long)blockIdx.x * lines;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) twl[i] = tw[i];
+  const int tot_lines = 3 * lines;
+  if (have_delta) {
+    // Hermitian-extend the two half spectra of each component pair into Z = A + i B.
+    for (int i = threadIdx.x; i < tot_lines * n1h; i += blockDim.x) {
+      const int k = i % n1h;
+      const int pl = i / n1h;                 // pair * lines + l
+      const int l = pl % lines, p = pl / lines;
+      const long long li = line0 + l;
+      T z0, z1;
+      if (li < nlines) {
+        const long long row = li * d.P;        // (i3 n2 + i2) P
+        T A = spec[(2 * p) * d.S + row + k];
+        T B = spec[(2 * p + 1) * d.S + row + k];
+        const bool selfconj = (k == 0) || (2 * k == n1);
+        if (selfconj) { A.y = 0; B.y = 0; }
+        z0.x = A.x - B.y; z0.y = A.y + B.x;     // Z[k] = A + iB
+        z1.x = A.x + B.y; z1.y = -A.y + B.x;    // Z[n-k] = conj(A) + i conj(B)
+      } else {
+        z0.x = z0.y = z1.x = z1.y = 0;
+      }
+      T* line = buf + pl * n1;
+      line[k] = z0;
+      if (k > 0 && 2 * k != n1) line[n1 - k] = z1;
+    }
+    __syncthreads();
+    buf = fft_lines<true>(bufa, bufb, twl, plan, LineLayout{tot_lines, 1, n1, false});
+  } else {
+    __syncthreads();
+  }
+  // eps += d_eps, sigma = C : eps, repack sigma pairs for the forward transform
+  for (int i = threadIdx.x; i < lines * n1; i += blockDim.x) {
+    const int x = i % n1, l = i / n1;
+    const long long li = line0 + l;
+    if (li >= nlines) continue;
+    const long long v = li * n1 + x;
+    R e[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + v];
+    if (have_delta) {
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const T z = buf[(p * lines + l) * n1 + x];
+        e[2 * p] += z.x;
+        e[2 * p + 1] += z.y;
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) eps[c * d.N + v] = e[c];
+    }
+    const R la = lam[v], m2 = (R)2 * mu[v];
+    const R ltr = la * (e[0] + e[1] + e[2]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      T z;
+      z.x = m2 * e[2 * p] + (p < 2 ? ltr : (R)0);        // 11, 33, 13
+      z.y = m2 * e[2 * p + 1] + (p == 0 ? ltr : (R)0);   // 22, 23, 12
+      buf[(p * lines + l) * n1 + x] = z;
+    }
+  }
+  __syncthreads();
+  buf = fft_lines<false>(buf, buf == bufa ? bufb : bufa, twl, plan, LineLayout{tot_lines, 1, n1, false});
+  // split Z = FFT(a + i b) into the half spectra of a and b
+  for (int i = threadIdx.x; i < tot_lines * n1h; i += blockDim.x) {
+    const int k = i % n1h;
+    const int pl = i / n1h;
+    const int l = pl % lines, p = pl / lines;
+    const long long li = line0 + l;
+    if (li >= nlines) continue;
+    const T* line = buf + pl * n1;
+    const T zk = line[k];
+    const T zn = line[(n1 - k) % n1];
+    T A, B;
+    A.x = (R)0.5 * (zk.x + zn.x); A.y = (R)0.5 * (zk.y - zn.y);
+    B.x = (R)0.5 * (zk.y + zn.y); B.y = (R)-0.5 * (zk.x - zn.x);
+    const long long row = li * d.P;
+    spec[(2 * p) * d.S + row + k] = A;
+    spec[(2 * p + 1) * d.S + row + k] = B;
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// pass_y: tile = all n2 rows x `cols` consecutive k1 columns of one component at fixed k3.
+// --------------------------------------------------------------------------------------------
+template <typename R, bool INV>
+__global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typename C<R>::T* __restrict__ tw,
+                              FftPlan plan, Dims d, int cols, const SolveState* __restrict__ st) {
+  typedef typename C<R>::T T;
+  if (st->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* buf = twl + d.n2;                       // [n2][cols], plus a ping-pong copy
+  T* buf2 = buf + d.n2 * cols;
+  const int k10 = blockIdx.x * cols;
+  const int k3 = blockIdx.y;
+  const int c = blockIdx.z;
+  for (int i = threadIdx.x; i < d.n2; i += blockDim.x) twl[i] = tw[i];
+  T* g = spec + c * d.S + (long long)k3 * d.n2 * d.P + k10;
+  for (int i = threadIdx.x; i < d.n2 * cols; i += blockDim.x) {
+    const int cc = i % cols, y = i / cols;
+    T v; v.x = 0; v.y = 0;
+    if (k10 + cc < d.n1h) v = g[(long long)y * d.P + cc];
+    buf[i] = v;
+  }
+  __syncthreads();
+  buf = fft_lines<INV>(buf, buf2, twl, plan, LineLayout{cols, cols, 1, true});
+  for (int i = threadIdx.x; i < d.n2 * cols; i += blockDim.x) {
+    const int cc = i % cols, y = i / cols;
+    if (k10 + cc < d.n1h) g[(long long)y * d.P + cc] = buf[i];
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// pass_z_gamma: tile = all n3 rows x `cols` k1 columns x 6 components at fixed k2.
+// smem layout [k3][comp][col] so that line (comp, col) has element stride 6 cols.
+// --------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const typename C<R>::T* __restrict__ tw,
+                                    FftPlan plan, Dims d, int cols, GammaParams<R> gp, double* __restrict__ partials,
+                                    SolveState* __restrict__ st) {
+  typedef typename C<R>::T T;
+  if (st->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* buf = twl + d.n3;                       // [n3][6][cols], plus a ping-pong copy
+  T* buf2 = buf + d.n3 * 6 * cols;
+  __shared__ double red[32];
+  const int k10 = blockIdx.x * cols;
+  const int k2 = blockIdx.y;
+  const int w6 = 6 * cols;
+  for (int i = threadIdx.x; i < d.n3; i += blockDim.x) twl[i] = tw[i];
+  for (int i = threadIdx.x; i < d.n3 * w6; i += blockDim.x) {
+    const int cc = i % cols, rest = i / cols;
+    const int comp = rest % 6, z = rest / 6;
+    T v; v.x = 0; v.y = 0;
+    if (k10 + cc < d.n1h) v = spec[comp * d.S + ((long long)z * d.n2 + k2) * d.P + k10 + cc];
+    buf[i] = v;
+  }
+  __syncthreads();
+  buf = fft_lines<false>(buf, buf2, twl, plan, LineLayout{w6, w6, 1, true});
+  T* other = (buf == buf2) ? buf2 - d.n3 * w6 : buf2;
+  // Green operator, residual and T(0)
+  R acc = 0;
+  const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
+  const R b2 = gp.B[1][k2], a2 = gp.A[1][k2];
+  for (int i = threadIdx.x; i < d.n3 * cols; i += blockDim.x) {
+    const int cc = i % cols, z = i / cols;
+    const int k1 = k10 + cc;
+    if (k1 >= d.n1h) continue;
+    T t[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = buf[(z * 6 + c) * cols + cc];
+    const R a1 = gp.A[0][k1], b1 = gp.B[0][k1];
+    const R a3 = gp.A[2][z], b3 = gp.B[2][z];
+    const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
+    const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
+    const bool ny3 = ((d.n3 & 1) == 0) && (2 * z == d.n3);
+    const bool self1 = (k1 == 0) || ny1;
+    // residual: stored point plus (for interior k1) its Hermitian partner, whose wave vector is
+    // -kt with the components on Nyquist axes 2, 3 negated back
+    R r2 = tk_norm2<R>(t, kt1, kt2, kt3);
+    if (!self1) {
+      if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(t, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
+      else r2 *= (R)2;
+    }
+    acc += r2;
+    if (k1 == 0 && k2 == 0 && z == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) st->T0[c] = (double)t[c].x;
+    }
+    T o[6];
+    gamma0_apply<R>(t, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
+    if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
+      T o2[6];
+      gamma0_apply<R>(t, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+  }
+  // deterministic block reduction of the residual partial (FP64 across threads)
+  double accd = (double)acc;
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+  buf = fft_lines<true>(buf, other, twl, plan, LineLayout{w6, w6, 1, true});
+  for (int i = threadIdx.x; i < d.n3 * w6; i += blockDim.x) {
+    const int cc = i % cols, rest = i / cols;
+    const int comp = rest % 6, z = rest / 6;
+    if (k10 + cc < d.n1h) spec[comp * d.S + ((long long)z * d.n2 + k2) * d.P + k10 + cc] = buf[i];
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// Launch configuration and host-side launchers (instantiated per precision in gfp_k64.cu / gfp_k32.cu)
+// --------------------------------------------------------------------------------------------
+struct LaunchCfg {
+  int x_lines, x_threads;
+  int y_cols, y_threads;
+  int z_cols, z_threads;
+  int z_blocks;  // number of pass_z CTAs (partials written)
+};
+
+template <typename R>
+struct Passes {
+  typedef typename C<R>::T T;
+  static cudaError_t setup();   // opt-in shared memory limits
+  static void pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, const R* lam, const R* mu, const T* tw,
+                     const FftPlan& plan, const Dims& d, int have_delta, const SolveState* st);
+  static void pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spec, const T* tw, const FftPlan& plan,
+                     const Dims& d, const SolveState* st);
+  static void pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw, const FftPlan& plan, const Dims& d,
+                     const GammaParams<R>& gp, double* partials, SolveState* st);
+};
+
+void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap);
+
+}  // namespace gfp

@@ -1,0 +1,270 @@
+"""Python binding of libgfp (ctypes): argument marshalling only; every step runs in the CUDA library.
+
+There is no CPU fallback: if the shared library is missing, importing works but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgfp.so")
+
+TD, PCD = 0, 1
+OPS = {"F": 0, "CD": 1, "ACD": 2, "HC": 3, "AHC": 4, "AFB_R": 5, "R": 5, "DGO": 6}
+FP64, MIXED = 0, 1
+
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSUPPORTED_SIZE", -3: "ERR_OOM", -4: "ERR_NOT_CONVERGED",
+          -5: "ERR_DIVERGED", -6: "ERR_DEVICE_TIMEOUT", -7: "ERR_CUDA", -8: "ERR_UNSUPPORTED"}
+
+
+class Scheme(ctypes.Structure):
+    _fields_ = [("disc", ctypes.c_int), ("op", ctypes.c_int), ("dgo_m", ctypes.c_int), ("prec", ctypes.c_int),
+                ("stop_rule", ctypes.c_int)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("residual", ctypes.c_double),
+                ("sigma_mean", ctypes.c_double * 6), ("status", ctypes.c_int),
+                ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int)]
+
+
+class GfpError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+
+
+_lib = None
+
+EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
+           "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
+           "gfp_time_passes")
+
+
+def lib():
+    """Load libgfp.so (built in-tree by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgfp.so not found at %s: build it with __graft_entry__.build(); "
+                           "there is no CPU fallback" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.gfp_create_grid.argtypes = [ip, ip, ip, dp, vp, ctypes.POINTER(vp)]
+    L.gfp_set_phases.argtypes = [vp, vp, vp, ip, vp]
+    L.gfp_solve.argtypes = [vp, ctypes.POINTER(Scheme), vp, dp, ip, ctypes.POINTER(_Result)]
+    L.gfp_get_strain.argtypes = [vp, vp, ip]
+    L.gfp_effective_stiffness.argtypes = [vp, ctypes.POINTER(Scheme), dp, ip, vp, vp]
+    L.gfp_grad.argtypes = [vp, ctypes.POINTER(Scheme), ip, ip, dp, ip, vp, vp, ip]
+    L.gfp_get_state.argtypes = [vp, vp, ctypes.POINTER(ip)]
+    L.gfp_set_state.argtypes = [vp, vp, ip]
+    L.gfp_destroy_grid.argtypes = [vp]
+    L.gfp_time_passes.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
+    L.gfp_error_string.argtypes = [ip]
+    L.gfp_error_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "gfp_error_string":
+            getattr(L, name).restype = ip
+    _lib = L
+    return L
+
+
+def _check(rc, where, ok=(0,)):
+    if rc not in ok:
+        raise GfpError(rc, where)
+    return rc
+
+
+def scheme(op="AFB_R", disc="TD", prec="FP64", dgo_m=0, stop_rule=0):
+    return Scheme(TD if disc == "TD" else PCD, OPS[op], int(dgo_m), FP64 if prec == "FP64" else MIXED,
+                  int(stop_rule))
+
+
+def _ptr_where(a):
+    """(pointer, where) for a numpy array (host) or a torch tensor (host or CUDA)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("expected a C-contiguous float64 array")
+        return a.ctypes.data_as(ctypes.c_void_p), 0
+    import torch
+    if not isinstance(a, torch.Tensor) or a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("expected a contiguous float64 tensor")
+    return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+
+
+class Result:
+    def __init__(self, r, status, history):
+        self.iters = r.iters
+        self.outer = r.outer
+        self.residual = r.residual
+        self.sigma_mean = np.array(list(r.sigma_mean))
+        self.status = status
+        self.converged = status == 0
+        self.history = history
+
+
+class Grid:
+    """A periodic n1 x n2 x n3 cell on the GPU (owns all device buffers of the solver)."""
+
+    def __init__(self, n1, n2, n3, h=1.0, stream=None):
+        self.shape = (n3, n2, n1)
+        self.N = n1 * n2 * n3
+        L = lib()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        self._h = ctypes.c_void_p()
+        _check(L.gfp_create_grid(n1, n2, n3, float(h), ctypes.c_void_p(stream), ctypes.byref(self._h)),
+               "gfp_create_grid")
+
+    def close(self):
+        if self._h:
+            lib().gfp_destroy_grid(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_phases(self, lam, mu, ref=None):
+        if isinstance(lam, np.ndarray):
+            lam = np.ascontiguousarray(lam, dtype=np.float64)
+            mu = np.ascontiguousarray(mu, dtype=np.float64)
+        pl, wl = _ptr_where(lam)
+        pm, wm = _ptr_where(mu)
+        if wl != wm:
+            raise ValueError("lambda and mu must live on the same side")
+        refp = None
+        if ref is not None:
+            self._ref = (ctypes.c_double * 2)(float(ref[0]), float(ref[1]))
+            refp = ctypes.cast(self._ref, ctypes.c_void_p)
+        _check(lib().gfp_set_phases(self._h, pl, pm, wl, refp), "gfp_set_phases")
+
+    def solve(self, sch, E, tol=1e-8, maxit=1000, history=False, raise_on_error=False):
+        E = (ctypes.c_double * 6)(*[float(v) for v in E])
+        r = _Result()
+        hist = None
+        if history:
+            hist = np.zeros(maxit)
+            r.residual_history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            r.history_cap = maxit
+        rc = lib().gfp_solve(self._h, ctypes.byref(sch), ctypes.cast(E, ctypes.c_void_p), float(tol), int(maxit),
+                             ctypes.byref(r))
+        if raise_on_error:
+            _check(rc, "gfp_solve")
+        elif rc not in (0, -4, -5):
+            raise GfpError(rc, "gfp_solve")
+        if hist is not None:
+            hist = hist[:r.iters]
+        return Result(r, rc, hist)
+
+    def strain(self, out=None):
+        if out is None:
+            out = np.empty((6,) + self.shape)
+        p, w = _ptr_where(out)
+        _check(lib().gfp_get_strain(self._h, p, w), "gfp_get_strain")
+        return out
+
+    def effective_stiffness(self, sch, tol=1e-8, maxit=1000):
+        C = np.zeros(36)
+        it = (ctypes.c_int * 6)()
+        rc = lib().gfp_effective_stiffness(self._h, ctypes.byref(sch), float(tol), int(maxit),
+                                           C.ctypes.data_as(ctypes.c_void_p), ctypes.cast(it, ctypes.c_void_p))
+        _check(rc, "gfp_effective_stiffness", ok=(0, -4))
+        return C.reshape(6, 6), list(it), rc
+
+    def grad(self, sch, I, J, tol=1e-10, maxit=5000, out_lambda=None, out_mu=None):
+        if out_lambda is None:
+            out_lambda = np.empty(self.shape)
+            out_mu = np.empty(self.shape)
+        pl, wl = _ptr_where(out_lambda)
+        pm, wm = _ptr_where(out_mu)
+        if wl != wm:
+            raise ValueError("outputs must live on the same side")
+        _check(lib().gfp_grad(self._h, ctypes.byref(sch), int(I), int(J), float(tol), int(maxit), pl, pm, wl),
+               "gfp_grad")
+        return out_lambda, out_mu
+
+    def time_passes(self, sch, iters):
+        """Mean per-kernel durations (ms) of pass_x, pass_y, pass_z_gamma, reduce, pass_y inverse."""
+        ms = np.zeros(5)
+        _check(lib().gfp_time_passes(self._h, ctypes.byref(sch), int(iters), ms.ctypes.data_as(ctypes.c_void_p)),
+               "gfp_time_passes")
+        return ms
+
+    def get_state(self):
+        eps = np.empty((6,) + self.shape)
+        it = ctypes.c_int()
+        _check(lib().gfp_get_state(self._h, eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it)), "gfp_get_state")
+        return eps, it.value
+
+    def set_state(self, eps, iters):
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        _check(lib().gfp_set_state(self._h, eps.ctypes.data_as(ctypes.c_void_p), int(iters)), "gfp_set_state")
+
+
+def solve(lam, mu, op="AFB_R", E=(0.01, 0, 0, 0, 0, 0), tol=1e-8, maxit=1000, disc="TD", prec="FP64", h=1.0,
+          ref=None, history=False):
+    """One-shot convenience: create a grid, set the phases, solve, return (Result, strain)."""
+    n3, n2, n1 = np.shape(lam)
+    g = Grid(n1, n2, n3, h)
+    try:
+        g.set_phases(lam, mu, ref)
+        r = g.solve(scheme(op, disc, prec), E, tol, maxit, history)
+        return r, g.strain()
+    finally:
+        g.close()
+
+
+def _autograd():
+    import torch
+
+    class GfpCeff(torch.autograd.Function):
+        """C_eff,IJ of a cell as a differentiable function of the voxel Lame fields (float64 tensors).
+
+        forward runs the solve of load J on the GPU; backward calls gfp_grad, whose adjoint field is the
+        forward solution of load I (Gamma is real and symmetric), and returns grad_out * dC/dlambda,
+        grad_out * dC/dmu.
+        """
+
+        @staticmethod
+        def forward(ctx, lam, mu, I, J, op, tol, maxit):
+            n3, n2, n1 = lam.shape
+            g = Grid(n1, n2, n3)
+            lam_c = lam.detach().contiguous()
+            mu_c = mu.detach().contiguous()
+            g.set_phases(lam_c, mu_c)
+            E = np.zeros(6)
+            E[J] = 1.0 if J < 3 else 0.5
+            r = g.solve(scheme(op), E, tol, maxit, raise_on_error=True)
+            ctx.grid = g
+            ctx.args = (I, J, op, tol, maxit)
+            return torch.tensor(r.sigma_mean[I], dtype=torch.float64, device=lam.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            I, J, op, tol, maxit = ctx.args
+            g = ctx.grid
+            shape = g.shape
+            dev = gout.device
+            dl = torch.empty(shape, dtype=torch.float64, device=dev)
+            dm = torch.empty(shape, dtype=torch.float64, device=dev)
+            g.grad(scheme(op), I, J, tol, maxit, dl, dm)
+            g.close()
+            return gout * dl, gout * dm, None, None, None, None, None
+
+    return GfpCeff
+
+
+def ceff_entry(lam, mu, I=0, J=0, op="AFB_R", tol=1e-10, maxit=5000):
+    """Differentiable C_eff,IJ (torch autograd; backward via the hand-written adjoint and contraction kernel)."""
+    return _autograd().apply(lam, mu, I, J, op, tol, maxit)
