@@ -133,6 +133,10 @@ int gfp_destroy_grid(gfp_grid g);
 /* Static message for a status code. */
 const char* gfp_error_string(int status);
 
+/* Detail of the last CUDA runtime failure seen by this thread (CUDA's message, code and source line),
+ * or an empty string.  The pointer stays valid until the thread's next failing call. */
+const char* gfp_last_error_detail(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -221,12 +221,21 @@ void build_tables(int op, int n, double h, std::vector<double>& A, std::vector<d
   }
 }
 
+thread_local char g_detail[256] = "";
+
+void note_error(cudaError_t e, int line) {
+  std::snprintf(g_detail, sizeof(g_detail), "%s (%d) at gfp_api.cu:%d", cudaGetErrorString(e), (int)e, line);
+}
+
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GFP_OK : (e == cudaErrorMemoryAllocation ? GFP_ERR_OOM : GFP_ERR_CUDA); }
 
-#define GFP_CU(call)                         \
-  do {                                       \
-    cudaError_t e_ = (call);                 \
-    if (e_ != cudaSuccess) return cuda_status(e_); \
+#define GFP_CU(call)                                  \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) {                          \
+      note_error(e_, __LINE__);                       \
+      return cuda_status(e_);                         \
+    }                                                 \
   } while (0)
 
 std::once_flag g_setup_once;
@@ -237,6 +246,7 @@ int global_setup() {
     g_setup_err = Passes<double>::setup();
     if (g_setup_err == cudaSuccess) g_setup_err = Passes<float>::setup();
   });
+  if (g_setup_err != cudaSuccess) note_error(g_setup_err, __LINE__);
   return cuda_status(g_setup_err);
 }
 
@@ -276,9 +286,11 @@ int ensure_hist(gfp_grid g, int cap) {
 
 void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta) {
   const Dims& d = g->d;
-  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, have_delta, g->st);
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+                         have_delta ? PX_DELTA : 0, nullptr, nullptr, g->st);
   Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
-  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st);
+  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+                         nullptr);
   launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, g->hist, g->hist_cap);
   Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
 }
@@ -356,6 +368,8 @@ bool scheme_ok(const gfp_scheme* sc) {
 // ------------------------------------------------------------------------------- C ABI
 extern "C" {
 
+const char* gfp_last_error_detail(void) { return g_detail; }
+
 const char* gfp_error_string(int status) {
   switch (status) {
     case GFP_OK: return "ok";
@@ -409,7 +423,7 @@ int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_gri
   A((void**)&g->scratch, sizeof(double) * 4 * 1024);
   A((void**)&g->bad, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&g->st_host, sizeof(SolveState));
-  if (e != cudaSuccess) { free_grid(g); return cuda_status(e); }
+  if (e != cudaSuccess) { note_error(e, __LINE__); free_grid(g); return cuda_status(e); }
   // twiddles w_n^j = e^{-2 pi i j / n}
   const double pi = 3.14159265358979323846;
   for (int r = 0; r < 3; ++r) {
@@ -582,11 +596,13 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
   double acc[5] = {0, 0, 0, 0, 0};
   for (int it = 0; it < iters; ++it) {
     GFP_CU(cudaEventRecord(ev[0], g->stream));
-    Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 1, g->st);
+    Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_DELTA,
+                           nullptr, nullptr, g->st);
     GFP_CU(cudaEventRecord(ev[1], g->stream));
     Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
     GFP_CU(cudaEventRecord(ev[2], g->stream));
-    Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st);
+    Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+                           nullptr);
     GFP_CU(cudaEventRecord(ev[3], g->stream));
     launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
     GFP_CU(cudaEventRecord(ev[4], g->stream));

@@ -50,32 +50,48 @@ struct GammaParams {
   int nyq_avg;         // average Gamma over the Hermitian partner on Nyquist planes (F, HC)
 };
 
-// Real isotropic Gamma0 applied to a symmetric complex tensor t (6 comps), times -scale:
-// out_ij = -scale [ (k_i v_j + k_j v_i) / (2 mu s) - c_lm k_i k_j (k.v) / s^2 ],  v = t k, s = |k|^2.
+// v = t kt for a symmetric complex tensor t (components 11,22,33,23,13,12) and a real vector kt
 template <typename R, typename T>
-__device__ __forceinline__ void gamma0_apply(const T t[6], R k1, R k2, R k3, R c_mu, R c_lm, R scale, T out[6]) {
+__device__ __forceinline__ void tk_vec(const T t[6], R k1, R k2, R k3, T& v1, T& v2, T& v3) {
+  v1.x = t[0].x * k1 + t[5].x * k2 + t[4].x * k3;  v1.y = t[0].y * k1 + t[5].y * k2 + t[4].y * k3;
+  v2.x = t[5].x * k1 + t[1].x * k2 + t[3].x * k3;  v2.y = t[5].y * k1 + t[1].y * k2 + t[3].y * k3;
+  v3.x = t[4].x * k1 + t[3].x * k2 + t[2].x * k3;  v3.y = t[4].y * k1 + t[3].y * k2 + t[2].y * k3;
+}
+
+// Real isotropic Gamma0(kt) applied to a tensor whose product with kt is v, times -scale:
+// out_ij = -scale [ (k_i v_j + k_j v_i) / (2 mu s) - c_lm k_i k_j (k.v) / s^2 ],  s = |kt|^2;
+// out = 0 where kt = 0 (k = 0 and the modes where the scheme's wave vector vanishes).
+template <typename R, typename T>
+__device__ __forceinline__ void gamma0_from_v(T v1, T v2, T v3, R k1, R k2, R k3, R c_mu, R c_lm, R scale, T out[6]) {
   const R s = k1 * k1 + k2 * k2 + k3 * k3;
   if (s == (R)0) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) { out[c].x = 0; out[c].y = 0; }
     return;
   }
-  T v1, v2, v3;
-  v1.x = t[0].x * k1 + t[5].x * k2 + t[4].x * k3;  v1.y = t[0].y * k1 + t[5].y * k2 + t[4].y * k3;
-  v2.x = t[5].x * k1 + t[1].x * k2 + t[3].x * k3;  v2.y = t[5].y * k1 + t[1].y * k2 + t[3].y * k3;
-  v3.x = t[4].x * k1 + t[3].x * k2 + t[2].x * k3;  v3.y = t[4].y * k1 + t[3].y * k2 + t[2].y * k3;
   const R is = (R)1 / s;
   const R a = c_mu * is * scale;               // scale / (2 mu s)
   T kv; kv.x = k1 * v1.x + k2 * v2.x + k3 * v3.x; kv.y = k1 * v1.y + k2 * v2.y + k3 * v3.y;
   const R b = c_lm * is * is * scale;
   T bkv; bkv.x = b * kv.x; bkv.y = b * kv.y;
-  // out = -(a (k_i v_j + k_j v_i) - k_i k_j bkv)
   out[0].x = -(a * 2 * k1 * v1.x - k1 * k1 * bkv.x); out[0].y = -(a * 2 * k1 * v1.y - k1 * k1 * bkv.y);
   out[1].x = -(a * 2 * k2 * v2.x - k2 * k2 * bkv.x); out[1].y = -(a * 2 * k2 * v2.y - k2 * k2 * bkv.y);
   out[2].x = -(a * 2 * k3 * v3.x - k3 * k3 * bkv.x); out[2].y = -(a * 2 * k3 * v3.y - k3 * k3 * bkv.y);
   out[3].x = -(a * (k2 * v3.x + k3 * v2.x) - k2 * k3 * bkv.x); out[3].y = -(a * (k2 * v3.y + k3 * v2.y) - k2 * k3 * bkv.y);
   out[4].x = -(a * (k1 * v3.x + k3 * v1.x) - k1 * k3 * bkv.x); out[4].y = -(a * (k1 * v3.y + k3 * v1.y) - k1 * k3 * bkv.y);
   out[5].x = -(a * (k1 * v2.x + k2 * v1.x) - k1 * k2 * bkv.x); out[5].y = -(a * (k1 * v2.y + k2 * v1.y) - k1 * k2 * bkv.y);
+}
+
+template <typename R, typename T>
+__device__ __forceinline__ void gamma0_apply(const T t[6], R k1, R k2, R k3, R c_mu, R c_lm, R scale, T out[6]) {
+  T v1, v2, v3;
+  tk_vec<R>(t, k1, k2, k3, v1, v2, v3);
+  gamma0_from_v<R>(v1, v2, v3, k1, k2, k3, c_mu, c_lm, scale, out);
+}
+
+template <typename T>
+__device__ __forceinline__ auto vnorm2(T v1, T v2, T v3) -> decltype(v1.x) {
+  return v1.x * v1.x + v1.y * v1.y + v2.x * v2.x + v2.y * v2.y + v3.x * v3.x + v3.y * v3.y;
 }
 
 // |T kt|^2 for a symmetric complex tensor (6 comps) and a real vector
@@ -93,10 +109,17 @@ __device__ __forceinline__ R tk_norm2(const T t[6], R k1, R k2, R k3) {
 // --------------------------------------------------------------------------------------------
 // pass_x: one CTA handles `lines` consecutive x1-lines (fixed i3, consecutive i2).
 // --------------------------------------------------------------------------------------------
+enum { PX_DELTA = 1, PX_ZERO = 2 };
+
+// flags: PX_DELTA adds the inverse x-transform of the spectrum (the previous increment) to the state;
+// PX_ZERO starts from a zero state (not read, written as zeros).  corr (FP32, may be null) is an
+// additive correction with FP64 mean corr_mean removed: state += corr - corr_mean (mixed-precision
+// refinement of the FP64 strain).
 template <typename R>
 __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict__ eps, const R* __restrict__ lam,
                               const R* __restrict__ mu, const typename C<R>::T* __restrict__ tw, FftPlan plan, Dims d,
-                              int lines, int have_delta, const SolveState* __restrict__ st) {
+                              int lines, int flags, const float* __restrict__ corr, const double* __restrict__ corr_mean,
+                              const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
   if (st->done) return;
   extern __shared__ unsigned char smem_raw[];
@@ -107,6 +130,8 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
   const int n1 = d.n1, n1h = d.n1h;
   const long long nlines = (long long)d.n2 * d.n3;
   const long long line0 = (long long)blockIdx.x * lines;
+  const bool have_delta = (flags & PX_DELTA) != 0;
+  const bool zero = (flags & PX_ZERO) != 0;
   for (int i = threadIdx.x; i < n1; i += blockDim.x) twl[i] = tw[i];
   const int tot_lines = 3 * lines;
   if (have_delta) {
@@ -137,15 +162,25 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
   } else {
     __syncthreads();
   }
-  // eps += d_eps, sigma = C : eps, repack sigma pairs for the forward transform
+  double cm[6];
+  if (corr) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cm[c] = corr_mean[c];
+  }
+  // state update, sigma = C : eps, repack sigma pairs for the forward transform
   for (int i = threadIdx.x; i < lines * n1; i += blockDim.x) {
     const int x = i % n1, l = i / n1;
     const long long li = line0 + l;
     if (li >= nlines) continue;
     const long long v = li * n1 + x;
     R e[6];
+    if (zero) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + v];
+      for (int c = 0; c < 6; ++c) e[c] = (R)0;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + v];
+    }
     if (have_delta) {
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
@@ -153,6 +188,12 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
         e[2 * p] += z.x;
         e[2 * p + 1] += z.y;
       }
+    }
+    if (corr) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] += (R)((double)corr[c * d.N + v] - cm[c]);
+    }
+    if (have_delta || zero || corr) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) eps[c * d.N + v] = e[c];
     }
@@ -222,10 +263,16 @@ __global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typenam
 // pass_z_gamma: tile = all n3 rows x `cols` k1 columns x 6 components at fixed k2.
 // smem layout [k3][comp][col] so that line (comp, col) has element stride 6 cols.
 // --------------------------------------------------------------------------------------------
+enum { PZ_GAMMA = 0, PZ_RESIDUAL = 1, PZ_INNER = 2 };
+
+// mode PZ_GAMMA: Delta E = -Gamma0(kt) T / N, residual, T(0), inverse z (the FP64 or FP32 iteration).
+// mode PZ_RESIDUAL: residual and T(0) only; stores v = T kt (FP32, [3][k3][k2][P]) as the source of
+// the inner iterations; no Green step, no inverse, the spectrum is not written back.
+// mode PZ_INNER: v = T kt + vsrc (the FP64 outer residual), residual of v, Delta E from v, inverse z.
 template <typename R>
 __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const typename C<R>::T* __restrict__ tw,
                                     FftPlan plan, Dims d, int cols, GammaParams<R> gp, double* __restrict__ partials,
-                                    SolveState* __restrict__ st) {
+                                    SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
   typedef typename C<R>::T T;
   if (st->done) return;
   extern __shared__ unsigned char smem_raw[];
@@ -264,20 +311,34 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
     const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
     const bool ny3 = ((d.n3 & 1) == 0) && (2 * z == d.n3);
     const bool self1 = (k1 == 0) || ny1;
+    const long long vi = ((long long)z * d.n2 + k2) * d.P + k1;
+    if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) st->T0[c] = (double)t[c].x;
+    }
+    T v1, v2, v3;
+    tk_vec<R>(t, kt1, kt2, kt3, v1, v2, v3);
+    if (mode == PZ_INNER) {
+      const float2 s1 = vsrc[vi], s2 = vsrc[d.S + vi], s3 = vsrc[2 * d.S + vi];
+      v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
+    }
     // residual: stored point plus (for interior k1) its Hermitian partner, whose wave vector is
     // -kt with the components on Nyquist axes 2, 3 negated back
-    R r2 = tk_norm2<R>(t, kt1, kt2, kt3);
+    R r2 = vnorm2(v1, v2, v3);
     if (!self1) {
       if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(t, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
       else r2 *= (R)2;
     }
     acc += r2;
-    if (k1 == 0 && k2 == 0 && z == 0) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) st->T0[c] = (double)t[c].x;
+    if (mode == PZ_RESIDUAL) {
+      float2 o1, o2, o3;
+      o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
+      o3.x = (float)v3.x; o3.y = (float)v3.y;
+      vsrc[vi] = o1; vsrc[d.S + vi] = o2; vsrc[2 * d.S + vi] = o3;
+      continue;
     }
     T o[6];
-    gamma0_apply<R>(t, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
+    gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
     if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
       T o2[6];
       gamma0_apply<R>(t, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
@@ -298,6 +359,7 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
+  if (mode == PZ_RESIDUAL) return;
   buf = fft_lines<true>(buf, other, twl, plan, LineLayout{w6, w6, 1, true});
   for (int i = threadIdx.x; i < d.n3 * w6; i += blockDim.x) {
     const int cc = i % cols, rest = i / cols;
@@ -321,11 +383,12 @@ struct Passes {
   typedef typename C<R>::T T;
   static cudaError_t setup();   // opt-in shared memory limits
   static void pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, const R* lam, const R* mu, const T* tw,
-                     const FftPlan& plan, const Dims& d, int have_delta, const SolveState* st);
+                     const FftPlan& plan, const Dims& d, int flags, const float* corr, const double* corr_mean,
+                     const SolveState* st);
   static void pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spec, const T* tw, const FftPlan& plan,
                      const Dims& d, const SolveState* st);
   static void pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw, const FftPlan& plan, const Dims& d,
-                     const GammaParams<R>& gp, double* partials, SolveState* st);
+                     const GammaParams<R>& gp, double* partials, SolveState* st, int mode, float2* vsrc);
 };
 
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap);

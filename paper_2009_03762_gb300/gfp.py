@@ -34,14 +34,17 @@ class _Result(ctypes.Structure):
 class GfpError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+        detail = ""
+        if code == -7 and _lib is not None:
+            detail = ": " + _lib.gfp_last_error_detail().decode(errors="replace")
+        super().__init__("%s failed: %s (%d)%s" % (where, STATUS.get(code, "?"), code, detail))
 
 
 _lib = None
 
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
-           "gfp_time_passes")
+           "gfp_time_passes", "gfp_last_error_detail")
 
 
 def lib():
@@ -66,8 +69,10 @@ def lib():
     L.gfp_time_passes.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
     L.gfp_error_string.argtypes = [ip]
     L.gfp_error_string.restype = ctypes.c_char_p
+    L.gfp_last_error_detail.argtypes = []
+    L.gfp_last_error_detail.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "gfp_error_string":
+        if name not in ("gfp_error_string", "gfp_last_error_detail"):
             getattr(L, name).restype = ip
     _lib = L
     return L
@@ -198,7 +203,7 @@ class Grid:
         """Mean per-kernel durations (ms) of pass_x, pass_y, pass_z_gamma, reduce, pass_y inverse."""
         ms = np.zeros(5)
         _check(lib().gfp_time_passes(self._h, ctypes.byref(sch), int(iters), ms.ctypes.data_as(ctypes.c_void_p)),
-               "gfp_time_passes")
+               "gfp_time_passes", "gfp_last_error_detail")
         return ms
 
     def get_state(self):
