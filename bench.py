@@ -82,12 +82,19 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def bytes_per_voxel_fp64(n):
-    """Algorithmic HBM bytes per voxel of each pass (FP64): pass_x reads the half spectrum, eps, lambda,
-    mu and writes eps and the half spectrum; the y and z passes read and write the half spectrum."""
+def bytes_per_voxel(n, prec):
+    """Algorithmic HBM bytes per voxel of each pass.  pass_x reads the half spectrum, the state and
+    lambda, mu and writes the state and the half spectrum; pass_y reads and writes the half spectrum;
+    pass_z_gamma does the same and, in the mixed inner iteration, also reads the FP64 source T kt
+    (3 complex FP32 per half-spectrum point)."""
     h = (n // 2 + 1) / n
-    spec = 6 * 16 * h
-    return {"pass_x": 2 * spec + 2 * 48 + 16, "pass_y": 2 * spec, "pass_z_gamma": 2 * spec}
+    if prec == "FP64":
+        spec = 6 * 16 * h
+        return {"pass_x": 2 * spec + 2 * 48 + 16, "pass_y": 2 * spec, "pass_z_gamma": 2 * spec,
+                "pass_y_inv": 2 * spec}
+    spec = 6 * 8 * h
+    return {"pass_x": 2 * spec + 2 * 24 + 8, "pass_y": 2 * spec, "pass_z_gamma": 2 * spec + 3 * 8 * h,
+            "pass_y_inv": 2 * spec}
 
 
 def run_gfp(args):
@@ -104,54 +111,78 @@ def run_gfp(args):
     lam_d = torch.from_numpy(lam).to(dev)
     mu_d = torch.from_numpy(mu).to(dev)
     g.set_phases(lam_d, mu_d)
-    sch = gfp.scheme(args.op, "PCD", "FP64")
+    prec = args.prec
+    sch = gfp.scheme(args.op, "PCD", prec)
     E = [0.0, 0.0, 0.0, 0.0, 0.0, 0.5]
     K, W = args.steps, args.warmup
-    # warm-up
-    g.solve(sch, E, 0.0, W)
+    g.solve(sch, E, 0.0, W)                   # warm-up
     torch.cuda.synchronize()
     clocks = Clocks()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    r = g.solve(sch, E, 0.0, K)      # exactly K iterations (tol = 0), inputs resident in HBM
+    r = g.solve(sch, E, 0.0, K)               # exactly K iterations (tol = 0), inputs resident in HBM
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    assert r.iters == K
+    assert r.iters == K, (r.iters, K)
     value = N * K / (ms * 1e-3)
-    # per-kernel durations on the same stream (dominant kernel for the roofline)
-    pass_ms = g.time_passes(sch, max(3, min(K, 10)))
+    # per-kernel durations on the same stream
+    pass_ms = g.time_passes(sch, max(3, min(K, 20)))
     names = ["pass_x", "pass_y", "pass_z_gamma", "reduce_eta", "pass_y_inv"]
-    bpv = bytes_per_voxel_fp64(n)
+    bpv = bytes_per_voxel(n, prec)
     shares = {nm: float(t) for nm, t in zip(names, pass_ms)}
-    dom = max(("pass_x", "pass_y", "pass_z_gamma"), key=lambda k: shares[k])
+    dom = max(("pass_x", "pass_y", "pass_z_gamma", "pass_y_inv"), key=lambda k: shares[k])
     peak, peak_kind = hbm_peak()
     achieved = bpv[dom] * N / (shares[dom] * 1e-3) / 1e9
+    it_ms = sum(shares.values())
+    it_bytes = sum(bpv.values()) * N
+    # time to the 1e-8 residual, mixed vs plain FP64, on the same cell
+    ttt = None
+    if args.ttt:
+        ttt = {}
+        for pr in ("MIXED", "FP64"):
+            s2 = gfp.scheme(args.op, "PCD", pr)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rr = g.solve(s2, E, 1e-8, args.ttt_maxit)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ttt[pr] = {"seconds": dt, "iters": rr.iters, "outer": rr.outer, "residual": rr.residual,
+                       "converged": rr.converged, "sigma_mean": [float(x) for x in rr.sigma_mean]}
+        sm, sf = np.array(ttt["MIXED"]["sigma_mean"]), np.array(ttt["FP64"]["sigma_mean"])
+        ttt["speedup"] = ttt["FP64"]["seconds"] / ttt["MIXED"]["seconds"]
+        ttt["sigma_mean_rel_diff"] = float(np.linalg.norm(sm - sf) / np.linalg.norm(sf))
     # end to end through the C ABI with host buffers: H2D of lambda, mu, K iterations, D2H of the strain
     eps_host = np.empty((6, n, n, n))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g.set_phases(lam, mu)
-    r2 = g.solve(sch, E, 0.0, K)
+    g.solve(sch, E, 0.0, K)
     g.strain(eps_host)
     t_e2e = time.perf_counter() - t0
     e2e = N * K / t_e2e
+    launches = 5 * K + (4 * 2 + 3 if prec == "MIXED" else 1)
     line = {
         "metric": METRIC, "value": value, "unit": "voxel-iterations/s", "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "random spheres %d^3, vf 0.25, r U[6,16], contrast 100, PCD, %s, FP64" % (n, args.op),
-                   "grid": n, "scheme": args.op, "precision": "FP64", "l2": "inputs larger than L2 (spectrum %.0f MB)"
-                   % (6 * 16 * (n // 2 + 1) * n * n / 1e6)},
+        "dtype": "f32+f64" if prec == "MIXED" else "f64", "data": "synthetic",
+        "config": {"workload": "random spheres %d^3, vf 0.25, r U[6,16], contrast 100, PCD %s, %s"
+                   % (n, args.op, "FP32 bulk / FP64 residual+refinement" if prec == "MIXED" else "FP64"),
+                   "grid": n, "scheme": args.op, "precision": prec,
+                   "l2": "inputs larger than L2 (spectrum %.0f MB)" % (6 * (8 if prec == "MIXED" else 16)
+                                                                      * (n // 2 + 1) * n * n / 1e6)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                     "bytes_per_voxel": bpv[dom]},
+                     "bytes_per_voxel": bpv[dom],
+                     "iteration": {"achieved": it_bytes / (it_ms * 1e-3) / 1e9, "frac": it_bytes / (it_ms * 1e-3) / 1e9 / peak,
+                                   "bytes_per_voxel": sum(bpv.values()), "ms": it_ms}},
         "pass_ms": shares,
+        "time_to_1e-8": ttt,
         "e2e": {"value": e2e, "unit": "voxel-iterations/s", "h2d_bytes_per_step": 2 * N * 8 / K,
                 "d2h_bytes_per_step": 6 * N * 8 / K},
-        "gpu_launches": 5 * K + 1,
+        "gpu_launches": launches,
         "clocks": clk,
     }
     g.close()
@@ -178,11 +209,14 @@ def cpu_cores():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gfp", choices=["gfp", "reference"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--op", default="AFB_R")
+    ap.add_argument("--prec", default="MIXED", choices=["MIXED", "FP64"])
+    ap.add_argument("--ttt", type=int, default=1, help="also time full solves to eta = 1e-8 (mixed and FP64)")
+    ap.add_argument("--ttt-maxit", type=int, default=3000)
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -125,7 +125,8 @@ int gfp_set_state(gfp_grid g, const double* eps_src, int iters);
 /* Measurement hook: runs `iters` iterations of the hot path on the grid's current strain (the
  * convergence test is disabled) with CUDA events around each kernel on the grid's stream, and returns
  * the mean duration in milliseconds of pass_x, pass_y (forward), pass_z_gamma, the residual reduction
- * and pass_y (inverse) in pass_ms[0..4].  The strain is modified as by `iters` iterations. */
+ * and pass_y (inverse) in pass_ms[0..4].  With scheme->prec = GFP_MIXED it first runs one FP64
+ * residual pass and then times the FP32 inner iterations.  The strain state is modified. */
 int gfp_time_passes(gfp_grid g, const gfp_scheme* scheme, int iters, double pass_ms[5]);
 
 int gfp_destroy_grid(gfp_grid g);

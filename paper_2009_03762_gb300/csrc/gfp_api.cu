@@ -106,6 +106,39 @@ __global__ void grad_contract_kernel(const double* eI, const double* eJ, long lo
   }
 }
 
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// Mean of the six FP32 correction components, accumulated in FP64 (stage 1: per-block partials).
+__global__ void corr_mean_partial_kernel(const float* __restrict__ corr, long long N, double* __restrict__ part) {
+  __shared__ double sh[6][256];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += (double)corr[c * N + i];
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// stage 2: one block, fixed order
+__global__ void corr_mean_final_kernel(const double* __restrict__ part, int nb, long long N, double* __restrict__ mean) {
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b * 6 + threadIdx.x];
+    mean[threadIdx.x] = s / (double)N;
+  }
+}
+
 }  // namespace gfp
 
 // ------------------------------------------------------------------------------- the grid
@@ -137,6 +170,21 @@ struct gfp_grid_s {
   double* eps_save = nullptr; // second strain field for gradients
   int state_iters = 0;
   bool resume_pending = false; // gfp_set_state was called: the next solve continues from it
+  // mixed precision (allocated on the first mixed solve)
+  LaunchCfg lc32;
+  float* lam32 = nullptr;
+  float* mu32 = nullptr;
+  float* eps32 = nullptr;      // FP32 correction state
+  float2* vsrc = nullptr;      // FP64 residual vector T kt as the inner source, [3][S]
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  float* tabA32[3] = {nullptr, nullptr, nullptr};
+  float* tabB32[3] = {nullptr, nullptr, nullptr};
+  SolveState* st_in = nullptr;
+  SolveState* st_in_host = nullptr;
+  double* cmean = nullptr;     // FP64 mean of the correction (6)
+  double* cpart = nullptr;     // its per-block partials
+  bool mixed_ready = false;
+  bool lam32_valid = false;
 };
 
 namespace {
@@ -256,7 +304,11 @@ void free_grid(gfp_grid g) {
   for (int r = 0; r < 3; ++r) { cudaFree(g->tw64[r]); cudaFree(g->tabA[r]); cudaFree(g->tabB[r]); }
   cudaFree(g->partials); cudaFree(g->st); cudaFree(g->hist); cudaFree(g->scratch); cudaFree(g->bad);
   cudaFree(g->eps_save);
+  cudaFree(g->lam32); cudaFree(g->mu32); cudaFree(g->eps32); cudaFree(g->vsrc);
+  for (int r = 0; r < 3; ++r) { cudaFree(g->tw32[r]); cudaFree(g->tabA32[r]); cudaFree(g->tabB32[r]); }
+  cudaFree(g->st_in); cudaFree(g->cmean); cudaFree(g->cpart);
   if (g->st_host) cudaFreeHost(g->st_host);
+  if (g->st_in_host) cudaFreeHost(g->st_in_host);
   delete g;
 }
 
@@ -268,6 +320,12 @@ int ensure_tables(gfp_grid g, int op) {
     build_tables(op, ns[r], g->h, A, B);
     GFP_CU(cudaMemcpyAsync(g->tabA[r], A.data(), sizeof(double) * ns[r], cudaMemcpyHostToDevice, g->stream));
     GFP_CU(cudaMemcpyAsync(g->tabB[r], B.data(), sizeof(double) * ns[r], cudaMemcpyHostToDevice, g->stream));
+    if (g->tabA32[r]) {
+      std::vector<float> Af(A.begin(), A.end()), Bf(B.begin(), B.end());
+      GFP_CU(cudaMemcpyAsync(g->tabA32[r], Af.data(), sizeof(float) * ns[r], cudaMemcpyHostToDevice, g->stream));
+      GFP_CU(cudaMemcpyAsync(g->tabB32[r], Bf.data(), sizeof(float) * ns[r], cudaMemcpyHostToDevice, g->stream));
+      GFP_CU(cudaStreamSynchronize(g->stream));
+    }
   }
   GFP_CU(cudaStreamSynchronize(g->stream));
   g->table_op = op;
@@ -354,6 +412,160 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
       if (nh > 0)
         GFP_CU(cudaMemcpy(out->residual_history, g->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
     }
+  }
+  return status;
+}
+
+int ensure_mixed(gfp_grid g) {
+  if (g->mixed_ready) return GFP_OK;
+  const Dims& d = g->d;
+  const int ns[3] = {g->n1, g->n2, g->n3};
+  g->lc32 = make_cfg(d, 8);
+  GFP_CU(cudaMalloc(&g->lam32, sizeof(float) * d.N));
+  GFP_CU(cudaMalloc(&g->mu32, sizeof(float) * d.N));
+  GFP_CU(cudaMalloc(&g->eps32, sizeof(float) * 6 * d.N));
+  GFP_CU(cudaMalloc(&g->vsrc, sizeof(float2) * 3 * d.S));
+  for (int r = 0; r < 3; ++r) {
+    GFP_CU(cudaMalloc(&g->tw32[r], sizeof(float2) * ns[r]));
+    GFP_CU(cudaMalloc(&g->tabA32[r], sizeof(float) * ns[r]));
+    GFP_CU(cudaMalloc(&g->tabB32[r], sizeof(float) * ns[r]));
+    std::vector<double2> tw(ns[r]);
+    GFP_CU(cudaMemcpy(tw.data(), g->tw64[r], sizeof(double2) * ns[r], cudaMemcpyDeviceToHost));
+    std::vector<float2> twf(ns[r]);
+    for (int j = 0; j < ns[r]; ++j) { twf[j].x = (float)tw[j].x; twf[j].y = (float)tw[j].y; }
+    GFP_CU(cudaMemcpy(g->tw32[r], twf.data(), sizeof(float2) * ns[r], cudaMemcpyHostToDevice));
+  }
+  GFP_CU(cudaMalloc(&g->st_in, sizeof(SolveState)));
+  GFP_CU(cudaMallocHost((void**)&g->st_in_host, sizeof(SolveState)));
+  GFP_CU(cudaMalloc(&g->cmean, sizeof(double) * 6));
+  GFP_CU(cudaMalloc(&g->cpart, sizeof(double) * 6 * 1024));
+  const int pz32 = g->lc32.z_blocks;
+  if (pz32 > g->np_max) {
+    cudaFree(g->partials);
+    g->partials = nullptr;
+    GFP_CU(cudaMalloc(&g->partials, sizeof(double) * pz32));
+    g->np_max = pz32;
+  }
+  g->table_op = -1;  // refill tables, now including the FP32 copies
+  g->mixed_ready = true;
+  return GFP_OK;
+}
+
+template <typename R>
+GammaParams<R> gamma_params(gfp_grid g, int op, const R* const* A, const R* const* B) {
+  GammaParams<R> gp;
+  for (int r = 0; r < 3; ++r) { gp.A[r] = A[r]; gp.B[r] = B[r]; }
+  gp.c_mu = (R)(1.0 / (2.0 * g->mu_h));
+  gp.c_lm = (R)((g->lam_h + g->mu_h) / (g->mu_h * (g->lam_h + 2.0 * g->mu_h)));
+  gp.invN = (R)(1.0 / (double)g->d.N);
+  gp.nyq_avg = (op == OP_F || op == OP_HC) ? 1 : 0;
+  return gp;
+}
+
+// FP64 outer pass: eps64 += corr - mean(corr) (if corr), sigma64 = C : eps64, forward 3D transform,
+// exact FP64 residual and mean stress, and v = T kt stored as the inner iterations' source.
+void residual_pass64(gfp_grid g, const GammaParams<double>& gp, bool with_corr) {
+  const Dims& d = g->d;
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0,
+                         with_corr ? g->eps32 : nullptr, g->cmean, g->st);
+  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_RESIDUAL,
+                         g->vsrc);
+  launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
+}
+
+// One FP32 inner iteration on the correction: delta += d_delta, sigma = C32 : delta, forward,
+// v = T kt + v64, Delta = -Gamma0(v) / N, inverse.
+void inner_iteration32(gfp_grid g, const GammaParams<float>& gp, int flags) {
+  const Dims& d = g->d;
+  float2* spec32 = reinterpret_cast<float2*>(g->spec);
+  Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, flags,
+                        nullptr, nullptr, g->st_in);
+  Passes<float>::pass_y(g->stream, g->lc32, false, spec32, g->tw32[1], g->plan[1], d, g->st_in);
+  Passes<float>::pass_z(g->stream, g->lc32, spec32, g->tw32[2], g->plan[2], d, gp, g->partials, g->st_in, PZ_INNER,
+                        g->vsrc);
+  launch_reduce_eta(g->stream, g->partials, g->lc32.z_blocks, g->st_in, nullptr, 0);
+  Passes<float>::pass_y(g->stream, g->lc32, true, spec32, g->tw32[1], g->plan[1], d, g->st_in);
+}
+
+const double kInnerReduction = 1e-4;  // target of one inner solve relative to the FP64 residual
+
+// Mixed precision: FP64 outer loop (exact residual, mean strain, refinement) around FP32 inner
+// iterations of the same Green-operator scheme on the correction.
+int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, int maxit, gfp_result* out) {
+  if (sc->op == OP_F || sc->op == OP_HC || sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
+  int rc = ensure_mixed(g);
+  if (rc) return rc;
+  rc = ensure_tables(g, sc->op);
+  if (rc) return rc;
+  const Dims& d = g->d;
+  const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+  if (!g->lam32_valid) {
+    to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->lam, g->lam32, d.N);
+    to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->mu, g->mu32, d.N);
+    g->lam32_valid = true;
+  }
+  const GammaParams<double> gp64 = gamma_params<double>(g, sc->op, g->tabA, g->tabB);
+  const GammaParams<float> gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
+  fill_eps_kernel<<<std::min<long long>(4096, (d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, d.N, E[0], E[1], E[2],
+                                                                                       E[3], E[4], E[5]);
+  SolveState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.maxit = 1 << 30;
+  s0.tol = tol;
+  s0.eta = INFINITY;
+  s0.eta_min = INFINITY;
+  *g->st_host = s0;
+  GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+  int inner_total = 0, outer = 0;
+  bool with_corr = false;
+  int status = GFP_ERR_NOT_CONVERGED;
+  while (true) {
+    residual_pass64(g, gp64, with_corr);
+    ++outer;
+    GFP_CU(cudaGetLastError());
+    GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
+    GFP_CU(cudaStreamSynchronize(g->stream));
+    const SolveState so = *g->st_host;
+    if (so.done == 1) { status = GFP_OK; break; }
+    if (so.done == 3) { status = GFP_ERR_DIVERGED; break; }
+    if (inner_total >= maxit) { status = GFP_ERR_NOT_CONVERGED; break; }
+    // inner solve of the correction equation from a zero correction
+    SolveState si = s0;
+    si.maxit = maxit - inner_total;
+    si.tol = std::max(0.5 * tol, kInnerReduction * so.eta);
+    for (int c = 0; c < 6; ++c) si.T0[c] = so.T0[c];
+    *g->st_in_host = si;
+    GFP_CU(cudaMemcpyAsync(g->st_in, g->st_in_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+    int launched = 0, chunk = 4;
+    while (launched < si.maxit) {
+      const int nb = std::min(chunk, si.maxit - launched);
+      for (int b = 0; b < nb; ++b) inner_iteration32(g, gp32, (launched + b) == 0 ? PX_ZERO : PX_DELTA);
+      launched += nb;
+      GFP_CU(cudaGetLastError());
+      GFP_CU(cudaMemcpyAsync(g->st_in_host, g->st_in, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
+      GFP_CU(cudaStreamSynchronize(g->stream));
+      if (g->st_in_host->done) break;
+      chunk = std::min(chunk * 2, 64);
+    }
+    inner_total += g->st_in_host->it;
+    if (g->st_in_host->done == 3) { status = GFP_ERR_DIVERGED; break; }
+    corr_mean_partial_kernel<<<cvb, 256, 0, g->stream>>>(g->eps32, d.N, g->cpart);
+    corr_mean_final_kernel<<<1, 32, 0, g->stream>>>(g->cpart, cvb, d.N, g->cmean);
+    // the next outer pass re-arms the FP64 state (it counts outer passes; never stops on maxit)
+    g->st_host->done = 0;
+    GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+    with_corr = true;
+  }
+  const SolveState& s = *g->st_host;
+  g->state_iters = inner_total;
+  if (out) {
+    out->iters = inner_total;
+    out->outer = outer;
+    out->residual = s.eta;
+    for (int c = 0; c < 6; ++c) out->sigma_mean[c] = s.T0[c] / (double)d.N;
+    out->status = status;
+    if (out->residual_history && out->history_cap > 0) out->residual_history[0] = s.eta;
   }
   return status;
 }
@@ -479,6 +691,7 @@ int gfp_set_phases(gfp_grid g, const double* lambda, const double* mu, int where
     g->mu_h = 0.5 * (q[2] + (-q[3]));
   }
   g->phases = true;
+  g->lam32_valid = false;
   return GFP_OK;
 }
 
@@ -486,7 +699,12 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   if (!g || !scheme_ok(sc) || !E || !(tol >= 0.0) || maxit < 1) return GFP_ERR_ARG;
   for (int c = 0; c < 6; ++c) if (!std::isfinite(E[c])) return GFP_ERR_ARG;
   if (!g->phases) return GFP_ERR_ARG;
-  if (sc->op == OP_DGO || sc->prec != GFP_FP64 || sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
+  if (sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
+  if (sc->prec == GFP_MIXED) {
+    g->resume_pending = false;
+    return solve_mixed(g, sc, E, tol, maxit, out);
+  }
+  if (sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
   const bool resume = g->resume_pending;
   g->resume_pending = false;
   return solve_fp64(g, sc, E, tol, maxit, out, resume);
@@ -573,40 +791,65 @@ int gfp_set_state(gfp_grid g, const double* eps_src, int iters) {
 
 int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[5]) {
   if (!g || !scheme_ok(sc) || iters < 1 || !pass_ms || !g->phases) return GFP_ERR_ARG;
-  if (sc->op == OP_DGO || sc->prec != GFP_FP64) return GFP_ERR_UNSUPPORTED;
-  int rc = ensure_tables(g, sc->op);
+  if (sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
+  const bool mixed = sc->prec == GFP_MIXED;
+  if (mixed && (sc->op == OP_F || sc->op == OP_HC)) return GFP_ERR_UNSUPPORTED;
+  int rc = mixed ? ensure_mixed(g) : GFP_OK;
   if (rc) return rc;
-  GammaParams<double> gp;
-  for (int r = 0; r < 3; ++r) { gp.A[r] = g->tabA[r]; gp.B[r] = g->tabB[r]; }
-  gp.c_mu = 1.0 / (2.0 * g->mu_h);
-  gp.c_lm = (g->lam_h + g->mu_h) / (g->mu_h * (g->lam_h + 2.0 * g->mu_h));
-  gp.invN = 1.0 / (double)g->d.N;
-  gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
+  rc = ensure_tables(g, sc->op);
+  if (rc) return rc;
+  const Dims& d = g->d;
+  const GammaParams<double> gp = gamma_params<double>(g, sc->op, g->tabA, g->tabB);
   SolveState s0;
   std::memset(&s0, 0, sizeof(s0));
-  s0.maxit = iters + 1;
+  s0.maxit = iters + 2;
   s0.tol = -1.0;  // never converges: every pass runs
   s0.eta = INFINITY;
   s0.eta_min = INFINITY;
   *g->st_host = s0;
   GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
-  const Dims& d = g->d;
+  GammaParams<float> gp32;
+  float2* spec32 = reinterpret_cast<float2*>(g->spec);
+  if (mixed) {
+    const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+    if (!g->lam32_valid) {
+      to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->lam, g->lam32, d.N);
+      to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->mu, g->mu32, d.N);
+      g->lam32_valid = true;
+    }
+    gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
+    residual_pass64(g, gp, false);  // fills the inner source
+    *g->st_in_host = s0;
+    GFP_CU(cudaMemcpyAsync(g->st_in, g->st_in_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+    inner_iteration32(g, gp32, PX_ZERO);
+  }
   cudaEvent_t ev[6];
   for (int i = 0; i < 6; ++i) GFP_CU(cudaEventCreate(&ev[i]));
   double acc[5] = {0, 0, 0, 0, 0};
   for (int it = 0; it < iters; ++it) {
     GFP_CU(cudaEventRecord(ev[0], g->stream));
-    Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_DELTA,
-                           nullptr, nullptr, g->st);
+    if (mixed)
+      Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d,
+                            PX_DELTA, nullptr, nullptr, g->st_in);
+    else
+      Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_DELTA,
+                             nullptr, nullptr, g->st);
     GFP_CU(cudaEventRecord(ev[1], g->stream));
-    Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    if (mixed) Passes<float>::pass_y(g->stream, g->lc32, false, spec32, g->tw32[1], g->plan[1], d, g->st_in);
+    else Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
     GFP_CU(cudaEventRecord(ev[2], g->stream));
-    Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
-                           nullptr);
+    if (mixed)
+      Passes<float>::pass_z(g->stream, g->lc32, spec32, g->tw32[2], g->plan[2], d, gp32, g->partials, g->st_in,
+                            PZ_INNER, g->vsrc);
+    else
+      Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+                             nullptr);
     GFP_CU(cudaEventRecord(ev[3], g->stream));
-    launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
+    if (mixed) launch_reduce_eta(g->stream, g->partials, g->lc32.z_blocks, g->st_in, nullptr, 0);
+    else launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
     GFP_CU(cudaEventRecord(ev[4], g->stream));
-    Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    if (mixed) Passes<float>::pass_y(g->stream, g->lc32, true, spec32, g->tw32[1], g->plan[1], d, g->st_in);
+    else Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
     GFP_CU(cudaEventRecord(ev[5], g->stream));
     GFP_CU(cudaEventSynchronize(ev[5]));
     for (int k = 0; k < 5; ++k) {
@@ -617,7 +860,8 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
   }
   for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
   for (int k = 0; k < 5; ++k) pass_ms[k] = acc[k] / iters;
-  return cuda_status(cudaGetLastError());
+  GFP_CU(cudaGetLastError());
+  return GFP_OK;
 }
 
 }  // extern "C"

@@ -203,7 +203,7 @@ class Grid:
         """Mean per-kernel durations (ms) of pass_x, pass_y, pass_z_gamma, reduce, pass_y inverse."""
         ms = np.zeros(5)
         _check(lib().gfp_time_passes(self._h, ctypes.byref(sch), int(iters), ms.ctypes.data_as(ctypes.c_void_p)),
-               "gfp_time_passes", "gfp_last_error_detail")
+               "gfp_time_passes")
         return ms
 
     def get_state(self):

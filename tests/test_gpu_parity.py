@@ -59,8 +59,8 @@ def test_parity_random_field(gfp, op, shape):
 
 @pytest.mark.parametrize("op", FDD)
 def test_parity_fixed_iterations_ragged(gfp, op):
-    """Exactly K iterations (tol = 0) on a 27 x 10 x 24 grid (radix 3 and ragged k1 tiles)."""
-    lam, mu = M.random_field(24, 10, 27, seed=9)
+    """Exactly K iterations (tol = 0) on a 24 x 6 x 27 grid (radix 3 and ragged k1 tiles)."""
+    lam, mu = M.random_field(24, 6, 27, seed=9)
     E = [0.0, 0.0, 0.0, 0.0, 0.0, 0.01]
     r, eps = gfp.solve(lam, mu, op, E, tol=0.0, maxit=7)
     ref = O.solve(lam, mu, op, E, max_iters_exact=7)
