@@ -189,6 +189,23 @@ def run_gfp(args):
     return line
 
 
+def passes_only(args):
+    """Set phases, one FP64 residual pass (mixed), then K timed iterations: the small profiling case."""
+    import torch
+    from paper_2009_03762_gb300 import gfp
+    n = args.n
+    lam, mu = workload(n)
+    g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
+    g.set_phases(lam, mu)
+    ms = g.time_passes(gfp.scheme(args.op, "PCD", args.prec), args.passes_only)
+    bpv = bytes_per_voxel(n, args.prec)
+    names = ["pass_x", "pass_y", "pass_z_gamma", "reduce_eta", "pass_y_inv"]
+    out = {"n": n, "prec": args.prec, "pass_ms": dict(zip(names, map(float, ms)))}
+    out["gbs"] = {k: bpv[k] * n ** 3 / (out["pass_ms"][k] * 1e-3) / 1e9 for k in bpv}
+    g.close()
+    return out
+
+
 def oracle_sample(n, op, iters):
     """Time the FP64 oracle as it stands on `iters` iterations of the same workload."""
     from oracle import gfp_oracle as O
@@ -219,6 +236,8 @@ def main():
     ap.add_argument("--ttt-maxit", type=int, default=3000)
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--passes-only", type=int, default=0,
+                    help="only time K iterations pass by pass (gfp_time_passes) and print them (profiling case)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -239,6 +258,9 @@ def main():
                                  "sample": "%d single iterations of a %d^3 cell" % (args.steps, args.oracle_n)},
                 "e2e": {"value": value, "unit": "voxel-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+    if args.passes_only:
+        print(json.dumps(passes_only(args)))
         return
     line = run_gfp(args)
     if not args.no_cpu_baseline and rank == 0:

@@ -818,8 +818,12 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
       g->lam32_valid = true;
     }
     gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
-    residual_pass64(g, gp, false);  // fills the inner source
-    *g->st_in_host = s0;
+    residual_pass64(g, gp, false);  // fills the inner source and T(0)
+    GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
+    GFP_CU(cudaStreamSynchronize(g->stream));
+    SolveState si = s0;
+    for (int c = 0; c < 6; ++c) si.T0[c] = g->st_host->T0[c];
+    *g->st_in_host = si;
     GFP_CU(cudaMemcpyAsync(g->st_in, g->st_in_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
     inner_iteration32(g, gp32, PX_ZERO);
   }

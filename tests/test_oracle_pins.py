@@ -231,7 +231,7 @@ def test_homogeneous_medium_converges_in_one_iteration(scheme):
 
 
 def _laminate_closed_form(lam1, mu1, E):
-    """Exact mean stress of a laminate along x1 (T constant across the layers, Sec. 2.1
+    """Exact mean stress of a laminate along x1 (T constant across the layers, Sec. 2.1, the 1D equilibrium argument
     generalised: sigma_11, sigma_12, sigma_13 uniform; eps_22, eps_33, eps_23 uniform)."""
     E11, E22, E33, E23, E13, E12 = E
     M_ = lam1 + 2 * mu1
