@@ -234,7 +234,7 @@ LaunchCfg make_cfg(const Dims& d, int eb) {
   while (yc > 1 && (long long)(d.n2 + 2 * yc * d.n2) * eb > budget) yc /= 2;
   c.y_cols = std::max(1, std::min(yc, d.n1h));
   c.y_threads = clampt(c.y_cols * d.n2 / 8);
-  int zc = 4;
+  int zc = d.n3 >= 512 ? 2 : 4;  // register-FFT z-pass: 6 zc (n3 / 16) threads <= 512
   while (zc > 1 && (long long)(d.n3 + 12 * zc * d.n3) * eb > budget) zc /= 2;
   c.z_cols = std::max(1, std::min(zc, d.n1h));
   c.z_threads = clampt(6 * c.z_cols * d.n3 / 8);

@@ -1,0 +1,398 @@
+// Register-resident line FFTs with compile-time lengths (sm_103a), and the hot-path passes built on
+// them.  Same transform as gfp_fft.cuh (Stockham stages, forward e^{-2 pi i jk/n}, unnormalised), but
+// each thread keeps E elements of a line in registers: the first stage reads global memory directly,
+// the last stage writes global memory directly, and consecutive stages exchange through shared
+// memory once.  All index arithmetic is compile-time except the thread's position in the line.
+#pragma once
+#include "gfp_kernels.cuh"
+
+namespace gfp {
+
+// Stage radices per length: E elements per thread, T = N / E threads per line; every radix divides E.
+template <int N> struct CPlan { static constexpr bool ok = false; };
+#define GFP_CPLAN(N_, E_, NST_, R0, R1, R2)                                                   \
+  template <> struct CPlan<N_> {                                                               \
+    static constexpr bool ok = true;                                                           \
+    static constexpr int N = N_, E = E_, T = N_ / E_, NST = NST_;                              \
+    __host__ __device__ static constexpr int R(int s) { return s == 0 ? R0 : (s == 1 ? R1 : R2); } \
+    __host__ __device__ static constexpr int Ns(int s) { return s == 0 ? 1 : (s == 1 ? R0 : R0 * R1); } \
+  };
+GFP_CPLAN(32, 8, 2, 8, 4, 1)
+GFP_CPLAN(64, 8, 2, 8, 8, 1)
+GFP_CPLAN(96, 24, 3, 8, 4, 3)
+GFP_CPLAN(128, 16, 2, 16, 8, 1)
+GFP_CPLAN(192, 24, 3, 8, 8, 3)
+GFP_CPLAN(256, 16, 2, 16, 16, 1)
+GFP_CPLAN(512, 16, 3, 16, 16, 2)
+#undef GFP_CPLAN
+
+// Element index read by input r of butterfly b at stage S (thread position t): j + r N / R, j = t + b T.
+template <int N, int S> __device__ __forceinline__ int cin_idx(int t, int b, int r) {
+  typedef CPlan<N> P;
+  return t + b * P::T + r * (N / P::R(S));
+}
+// Element index written by output r of butterfly b at stage S: (j / Ns) Ns R + j % Ns + r Ns.
+template <int N, int S> __device__ __forceinline__ int cout_idx(int t, int b, int r) {
+  typedef CPlan<N> P;
+  constexpr int R = P::R(S), Ns = P::Ns(S);
+  const int j = t + b * P::T;
+  return (j / Ns) * Ns * R + (j % Ns) + r * Ns;
+}
+
+// Twiddle and butterflies of stage S for the thread's E / R butterflies.
+template <int N, int S, bool INV, typename T>
+__device__ __forceinline__ void cstage(T* v, int t, const T* __restrict__ tw) {
+  typedef CPlan<N> P;
+  constexpr int R = P::R(S), Ns = P::Ns(S), NB = P::E / R, stride = N / (Ns * R);
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (S > 0) {
+      const int k = (t + b * P::T) % Ns;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        T w = tw[r * k * stride];
+        if (INV) w.y = -w.y;
+        v[b * R + r] = cmul(v[b * R + r], w);
+      }
+    }
+    Dft<R, INV, T>::run(v + b * R);
+  }
+}
+
+// Line buffer in shared memory with an element stride and an optional pad of one element per 16
+// (line-major buffers, to spread the strided Stockham writes over the banks).
+template <typename T, bool PAD>
+struct SLine {
+  T* base;
+  int es;
+  __device__ __forceinline__ T& operator[](int e) const { return base[(PAD ? e + (e >> 4) : e) * es]; }
+};
+
+template <int N, int S, bool INV, typename T, bool PAD>
+__device__ __forceinline__ void cexchange(T* v, SLine<T, PAD> sm, int t) {
+  typedef CPlan<N> P;
+  constexpr int R = P::R(S), R1 = P::R(S + 1);
+#pragma unroll
+  for (int b = 0; b < P::E / R; ++b)
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[cout_idx<N, S>(t, b, r)] = v[b * R + r];
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < P::E / R1; ++b)
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[b * R1 + r] = sm[cin_idx<N, S + 1>(t, b, r)];
+  __syncthreads();
+}
+
+// Full transform of one line held as v[b R0 + r] = x[cin_idx<N,0>(t,b,r)]; on return
+// v[b RL + r] = X[cout_idx<N,NST-1>(t,b,r)] = X[t + b T + r N / RL].  Every thread of the block
+// must call it (it synchronises).
+template <int N, bool INV, typename T, bool PAD>
+__device__ __forceinline__ void cfft(T* v, SLine<T, PAD> sm, int t, const T* __restrict__ tw) {
+  typedef CPlan<N> P;
+  cstage<N, 0, INV>(v, t, tw);
+  if constexpr (P::NST > 1) {
+    cexchange<N, 0, INV>(v, sm, t);
+    cstage<N, 1, INV>(v, t, tw);
+  }
+  if constexpr (P::NST > 2) {
+    cexchange<N, 1, INV>(v, sm, t);
+    cstage<N, 2, INV>(v, t, tw);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass_y: CTA = C columns of k1 x all n2 rows of one component at fixed k3; thread = (column, t).
+// ------------------------------------------------------------------------------------------------
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restrict__ spec,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d, int cols,
+                                                       const SolveState* __restrict__ st) {
+  typedef typename C<R>::T T;
+  typedef CPlan<N> P;
+  if (st->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* buf = twl + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
+  const int col = threadIdx.x % cols, t = threadIdx.x / cols;
+  const int k1 = blockIdx.x * cols + col;
+  const bool live = k1 < d.n1h;
+  T* g = spec + blockIdx.z * d.S + (long long)blockIdx.y * d.n2 * d.P + k1;
+  T v[P::E];
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) {
+      T x; x.x = 0; x.y = 0;
+      if (live) x = g[(long long)cin_idx<N, 0>(t, b, r) * d.P];
+      v[b * P::R(0) + r] = x;
+    }
+  __syncthreads();
+  cfft<N, INV>(v, SLine<T, false>{buf + col, cols}, t, twl);
+  constexpr int RL = P::R(P::NST - 1);
+  if (live) {
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) g[(long long)cout_idx<N, P::NST - 1>(t, b, r) * d.P] = v[b * RL + r];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass_z_gamma: CTA = C columns x 6 components x all n3 rows at fixed k2; line = (comp, col).
+// Same modes as the generic kernel (PZ_GAMMA, PZ_RESIDUAL, PZ_INNER).
+// ------------------------------------------------------------------------------------------------
+template <typename R, int N>
+__global__ void __launch_bounds__(512) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d, int cols,
+                                                       GammaParams<R> gp, double* __restrict__ partials,
+                                                       SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
+  typedef typename C<R>::T T;
+  typedef CPlan<N> P;
+  if (st->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* buf = twl + N;                          // [k3][6][cols]
+  __shared__ double red[32];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
+  const int w6 = 6 * cols;
+  const int l = threadIdx.x % w6, t = threadIdx.x / w6;
+  const int comp = l / cols, col = l % cols;
+  const int k10 = blockIdx.x * cols;
+  const int k2 = blockIdx.y;
+  const bool live = k10 + col < d.n1h;
+  T* g = spec + comp * d.S + (long long)k2 * d.P + k10 + col;
+  const long long zs = (long long)d.n2 * d.P;
+  T v[P::E];
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) {
+      T x; x.x = 0; x.y = 0;
+      if (live) x = g[cin_idx<N, 0>(t, b, r) * zs];
+      v[b * P::R(0) + r] = x;
+    }
+  __syncthreads();
+  const SLine<T, false> sl{buf + l, w6};
+  cfft<N, false>(v, sl, t, twl);
+  constexpr int RL = P::R(P::NST - 1);
+#pragma unroll
+  for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  __syncthreads();
+  // Green operator, residual and T(0) per (k3, column)
+  R acc = 0;
+  const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
+  const R b2 = gp.B[1][k2], a2 = gp.A[1][k2];
+  for (int i = threadIdx.x; i < N * cols; i += blockDim.x) {
+    const int cc = i % cols, z = i / cols;
+    const int k1 = k10 + cc;
+    if (k1 >= d.n1h) continue;
+    T tt[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tt[c] = buf[(z * 6 + c) * cols + cc];
+    const R a1 = gp.A[0][k1], b1 = gp.B[0][k1];
+    const R a3 = gp.A[2][z], b3 = gp.B[2][z];
+    const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
+    const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
+    const bool ny3 = (2 * z == N);
+    const bool self1 = (k1 == 0) || ny1;
+    const long long vi = ((long long)z * d.n2 + k2) * d.P + k1;
+    if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
+    }
+    T v1, v2, v3;
+    tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
+    if (mode == PZ_INNER) {
+      const float2 s1 = vsrc[vi], s2 = vsrc[d.S + vi], s3 = vsrc[2 * d.S + vi];
+      v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
+    }
+    R r2 = vnorm2(v1, v2, v3);
+    if (!self1) {
+      if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(tt, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
+      else r2 *= (R)2;
+    }
+    acc += r2;
+    if (mode == PZ_RESIDUAL) {
+      float2 o1, o2, o3;
+      o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
+      o3.x = (float)v3.x; o3.y = (float)v3.y;
+      vsrc[vi] = o1; vsrc[d.S + vi] = o2; vsrc[2 * d.S + vi] = o3;
+      continue;
+    }
+    T o[6];
+    gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
+    if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
+      T o2[6];
+      gamma0_apply<R>(tt, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+  }
+  double accd = (double)acc;
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+  if (mode == PZ_RESIDUAL) return;
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) v[b * P::R(0) + r] = sl[cin_idx<N, 0>(t, b, r)];
+  __syncthreads();
+  cfft<N, true>(v, sl, t, twl);
+  if (live) {
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) g[cout_idx<N, P::NST - 1>(t, b, r) * zs] = v[b * RL + r];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass_x: CTA = `lines` x1-lines (consecutive i2 at fixed i3) x 3 component pairs; thread = (pair
+// line, t).  Same flags and correction as the generic kernel.
+// ------------------------------------------------------------------------------------------------
+template <typename R, int N>
+__global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restrict__ spec, R* __restrict__ eps,
+                                                       const R* __restrict__ lam, const R* __restrict__ mu,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d, int lines,
+                                                       int flags, const float* __restrict__ corr,
+                                                       const double* __restrict__ corr_mean,
+                                                       const SolveState* __restrict__ st) {
+  typedef typename C<R>::T T;
+  typedef CPlan<N> P;
+  if (st->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* buf = twl + N;                          // [3 lines][N + N/16] (padded line-major)
+  constexpr int LP = N + N / 16;
+  constexpr int NH = N / 2 + 1;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
+  const long long nlines = (long long)d.n2 * d.n3;
+  const long long line0 = (long long)blockIdx.x * lines;
+  const int t = threadIdx.x % P::T, fl = threadIdx.x / P::T;   // fl = pair * lines + l
+  const int p = fl / lines, l = fl % lines;
+  const long long li = line0 + l;
+  const bool live = (fl < 3 * lines) && (li < nlines);
+  const bool have_delta = (flags & PX_DELTA) != 0;
+  const bool zero = (flags & PX_ZERO) != 0;
+  const SLine<T, true> sl{buf + fl * LP, 1};
+  T v[P::E];
+  if (have_delta) {
+    const T* A = spec + (2 * p) * d.S + li * d.P;
+    const T* B = spec + (2 * p + 1) * d.S + li * d.P;
+#pragma unroll
+    for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+      for (int r = 0; r < P::R(0); ++r) {
+        const int x = cin_idx<N, 0>(t, b, r);
+        T z; z.x = 0; z.y = 0;
+        if (live) {
+          const int k = x < NH ? x : N - x;
+          T a = A[k], bb = B[k];
+          if (k == 0 || 2 * k == N) { a.y = 0; bb.y = 0; }
+          if (x < NH) { z.x = a.x - bb.y; z.y = a.y + bb.x; }      // A + iB
+          else { z.x = a.x + bb.y; z.y = -a.y + bb.x; }            // conj(A) + i conj(B)
+        }
+        v[b * P::R(0) + r] = z;
+      }
+    __syncthreads();
+    cfft<N, true>(v, sl, t, twl);
+    constexpr int RL = P::R(P::NST - 1);
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  }
+  __syncthreads();
+  double cm[6];
+  if (corr) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cm[c] = corr_mean[c];
+  }
+  for (int i = threadIdx.x; i < lines * N; i += blockDim.x) {
+    const int x = i % N, ll = i / N;
+    const long long lj = line0 + ll;
+    if (lj >= nlines) continue;
+    const long long vv = lj * N + x;
+    const int px = x + (x >> 4);
+    R e[6];
+    if (zero) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] = (R)0;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + vv];
+    }
+    if (have_delta) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const T z = buf[(q * lines + ll) * LP + px];
+        e[2 * q] += z.x;
+        e[2 * q + 1] += z.y;
+      }
+    }
+    if (corr) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] += (R)((double)corr[c * d.N + vv] - cm[c]);
+    }
+    if (have_delta || zero || corr) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) eps[c * d.N + vv] = e[c];
+    }
+    const R la = lam[vv], m2 = (R)2 * mu[vv];
+    const R ltr = la * (e[0] + e[1] + e[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T z;
+      z.x = m2 * e[2 * q] + (q < 2 ? ltr : (R)0);        // 11, 33, 13
+      z.y = m2 * e[2 * q + 1] + (q == 0 ? ltr : (R)0);   // 22, 23, 12
+      buf[(q * lines + ll) * LP + px] = z;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) v[b * P::R(0) + r] = sl[cin_idx<N, 0>(t, b, r)];
+  __syncthreads();
+  cfft<N, false>(v, sl, t, twl);
+  {
+    constexpr int RL = P::R(P::NST - 1);
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  }
+  __syncthreads();
+  // split Z = FFT(a + i b) into the half spectra of a and b
+  for (int i = threadIdx.x; i < 3 * lines * NH; i += blockDim.x) {
+    const int k = i % NH, f = i / NH;
+    const int q = f / lines, ll = f % lines;
+    const long long lj = line0 + ll;
+    if (lj >= nlines) continue;
+    const T* line = buf + f * LP;
+    const int kn = (N - k) % N;
+    const T zk = line[k + (k >> 4)];
+    const T zn = line[kn + (kn >> 4)];
+    T A, B;
+    A.x = (R)0.5 * (zk.x + zn.x); A.y = (R)0.5 * (zk.y - zn.y);
+    B.x = (R)0.5 * (zk.y + zn.y); B.y = (R)-0.5 * (zk.x - zn.x);
+    const long long row = lj * d.P;
+    spec[(2 * q) * d.S + row + k] = A;
+    spec[(2 * q + 1) * d.S + row + k] = B;
+  }
+}
+
+}  // namespace gfp

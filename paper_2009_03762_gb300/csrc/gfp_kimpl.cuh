@@ -1,8 +1,12 @@
 // Launchers of the hot-path passes for one precision (included by gfp_k64.cu and gfp_k32.cu).
+// Grid sizes with a compile-time FFT plan (CPlan) use the register-resident kernels of
+// gfp_fftc.cuh; every other 2^a 3^b size uses the generic shared-memory Stockham kernels.
 #pragma once
-#include "gfp_kernels.cuh"
+#include "gfp_fftc.cuh"
 
 namespace gfp {
+
+#define GFP_FOR_CSIZES(X) X(32) X(64) X(96) X(128) X(192) X(256) X(512)
 
 template <typename R>
 cudaError_t Passes<R>::setup() {
@@ -11,13 +15,43 @@ cudaError_t Passes<R>::setup() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_gamma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+#define GFP_SET(N)                                                                                          \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_x_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  GFP_FOR_CSIZES(GFP_SET)
+#undef GFP_SET
   return e;
+}
+
+// lines per CTA of the compile-time x-pass: at most 512 threads (3 pair-lines x T each)
+template <int N> inline int cx_lines() { return std::max(1, std::min(16, 512 / (3 * CPlan<N>::T))); }
+
+template <typename R, int N>
+inline void launch_x_c(cudaStream_t s, typename C<R>::T* spec, R* eps, const R* lam, const R* mu,
+                       const typename C<R>::T* tw, const Dims& d, int flags, const float* corr, const double* corr_mean,
+                       const SolveState* st) {
+  typedef typename C<R>::T T;
+  const int lines = cx_lines<N>();
+  const long long nlines = (long long)d.n2 * d.n3;
+  const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
+  const size_t sm = sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16));
+  pass_x_c_kernel<R, N><<<blocks, 3 * lines * CPlan<N>::T, sm, s>>>(spec, eps, lam, mu, tw, d, lines, flags, corr,
+                                                                     corr_mean, st);
 }
 
 template <typename R>
 void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, const R* lam, const R* mu, const T* tw,
                        const FftPlan& plan, const Dims& d, int flags, const float* corr, const double* corr_mean,
                        const SolveState* st) {
+  switch (d.n1) {
+#define GFP_CASE(N) \
+    case N: launch_x_c<R, N>(s, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, st); return;
+    GFP_FOR_CSIZES(GFP_CASE)
+#undef GFP_CASE
+    default: break;
+  }
   const long long nlines = (long long)d.n2 * d.n3;
   const unsigned blocks = (unsigned)((nlines + lc.x_lines - 1) / lc.x_lines);
   const size_t sm = sizeof(T) * (size_t)(d.n1 + 6 * lc.x_lines * d.n1);
@@ -29,6 +63,19 @@ template <typename R>
 void Passes<R>::pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spec, const T* tw, const FftPlan& plan,
                        const Dims& d, const SolveState* st) {
   dim3 grid((d.n1h + lc.y_cols - 1) / lc.y_cols, d.n3, 6);
+  switch (d.n2) {
+#define GFP_CASE(N)                                                                                 \
+    case N: {                                                                                       \
+      const size_t smc = sizeof(T) * (size_t)(N + N * lc.y_cols);                                   \
+      const int th = lc.y_cols * CPlan<N>::T;                                                       \
+      if (inverse) pass_y_c_kernel<R, N, true><<<grid, th, smc, s>>>(spec, tw, d, lc.y_cols, st);   \
+      else pass_y_c_kernel<R, N, false><<<grid, th, smc, s>>>(spec, tw, d, lc.y_cols, st);          \
+      return;                                                                                       \
+    }
+    GFP_FOR_CSIZES(GFP_CASE)
+#undef GFP_CASE
+    default: break;
+  }
   const size_t sm = sizeof(T) * (size_t)(d.n2 + 2 * lc.y_cols * d.n2);
   if (inverse) pass_y_kernel<R, true><<<grid, lc.y_threads, sm, s>>>(spec, tw, plan, d, lc.y_cols, st);
   else pass_y_kernel<R, false><<<grid, lc.y_threads, sm, s>>>(spec, tw, plan, d, lc.y_cols, st);
@@ -38,6 +85,18 @@ template <typename R>
 void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw, const FftPlan& plan, const Dims& d,
                        const GammaParams<R>& gp, double* partials, SolveState* st, int mode, float2* vsrc) {
   dim3 grid((d.n1h + lc.z_cols - 1) / lc.z_cols, d.n2, 1);
+  switch (d.n3) {
+#define GFP_CASE(N)                                                                                           \
+    case N: {                                                                                                 \
+      const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols);                                        \
+      const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
+      pass_z_c_kernel<R, N><<<grid, th, smc, s>>>(spec, tw, d, lc.z_cols, gp, partials, st, mode, vsrc);      \
+      return;                                                                                                 \
+    }
+    GFP_FOR_CSIZES(GFP_CASE)
+#undef GFP_CASE
+    default: break;
+  }
   const size_t sm = sizeof(T) * (size_t)(d.n3 + 12 * lc.z_cols * d.n3);
   pass_z_gamma_kernel<R><<<grid, lc.z_threads, sm, s>>>(spec, tw, plan, d, lc.z_cols, gp, partials, st, mode, vsrc);
 }

@@ -181,3 +181,18 @@ def test_gradient_matches_oracle_closed_form_and_fd(gfp):
     fl, fm = O.gradient_fd(lam, mu, "AFB_R", 0, 0, vox, rel_step=1e-5, tol=1e-13)
     np.testing.assert_allclose(dl.ravel()[vox], fl, rtol=1e-5)
     np.testing.assert_allclose(dm.ravel()[vox], fm, rtol=1e-5)
+
+
+@pytest.mark.parametrize("shape", [(32, 64, 96), (96, 32, 64), (64, 96, 32), (128, 32, 192), (192, 128, 32),
+                                   (32, 192, 128), (256, 16, 32), (32, 256, 16), (16, 32, 256), (512, 8, 16),
+                                   (16, 512, 8), (8, 16, 512)])
+@pytest.mark.parametrize("op", ["F", "AFB_R"])
+def test_parity_register_fft_sizes(gfp, shape, op):
+    """Every length with a compile-time FFT plan, on every axis: three iterations element by element."""
+    n3, n2, n1 = shape
+    lam, mu = M.random_field(n1, n2, n3, seed=13)
+    E = [0.003, -0.002, 0.004, 0.001, 0.002, 0.005]
+    r, eps = gfp.solve(lam, mu, op, E, tol=0.0, maxit=3)
+    ref = O.solve(lam, mu, op, E, max_iters_exact=3)
+    assert _rel(eps, ref.eps) <= REL
+    assert _rel(r.sigma_mean, ref.sigma_mean) <= REL
