@@ -131,6 +131,27 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* scheme, int iters, double pass
 
 int gfp_destroy_grid(gfp_grid g);
 
+/* Allocation-free solve, for callers that cannot allocate GPU memory themselves, e.g. code that runs
+ * where device memory is owned and pre-reserved by a host framework or pool, or where the device-wide
+ * synchronisation of cudaMalloc/cudaFree would stall other work.  The paper has no counterpart: this
+ * is gfp_solve (FP64, finite-difference schemes, residual stopping rule) without a grid handle.
+ *   lambda, mu  device pointers, [n3][n2][n1] float64 (read);
+ *   eps         device pointer, 6 x [n3][n2][n1] float64: the solver state and the output strain;
+ *   ref_lambda_mu  host pointer to (lambda_H, mu_H), or NULL for 1/2 (min + max) of each constant;
+ *   cuda_stream    stream for all work (NULL = legacy default stream).
+ * It allocates nothing: its scratch (spectrum, tables, residual partials, state) lives in one
+ * file-scope device array of 8 MiB (8388608 bytes) that every GPU loading the library holds until the
+ * process exits.  A grid whose scratch does not fit (about 6 x 16 x (n1/2 + 1) x n2 x n3 bytes plus
+ * a few KB; 48^3 fits, 64^3 does not) is rejected with GFP_ERR_UNSUPPORTED_SIZE and a message in
+ * gfp_last_error_detail().  The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  All calls share the array
+ * and the previous call's contents stay in it (the solve clears what it needs), so calls that overlap
+ * on the GPU -- concurrent streams, or threads -- race and must be serialised by the caller.
+ * DGO and mixed precision return GFP_ERR_UNSUPPORTED. */
+int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, const double* mu,
+                      const double* ref_lambda_mu, const gfp_scheme* scheme, const double E_macro[6], double tol,
+                      int maxit, double* eps, gfp_result* out, void* cuda_stream);
+
 /* Static message for a status code. */
 const char* gfp_error_string(int status);
 

@@ -577,6 +577,82 @@ bool scheme_ok(const gfp_scheme* sc) {
 
 }  // namespace
 
+// ------------------------------------------------------------------------------- allocation-free solve
+// Scratch of gfp_solve_noalloc.  It is a file-scope device array, so every GPU that loads this
+// library holds it until the process exits, and every call of the entry point shares it.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+const int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch on the current device (looked up once per device).  In host code
+// g_noalloc_scratch only names a host-side stand-in, so kernels must be given this address instead.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  GFP_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return GFP_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    GFP_CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GFP_OK;
+}
+
+// Same stage radices as make_plan, without heap storage.
+FftPlan make_plan_fixed(int n) {
+  FftPlan p;
+  p.n = n;
+  p.nst = 0;
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  int n16 = a / 4;
+  const int r = a % 4;
+  int tail[2] = {0, 0}, nt = 0;
+  if (r == 1 && n16 > 0) { n16 -= 1; tail[nt++] = 8; tail[nt++] = 4; }
+  else if (r == 1) tail[nt++] = 2;
+  else if (r == 2) tail[nt++] = 4;
+  else if (r == 3) tail[nt++] = 8;
+  for (int i = 0; i < n16; ++i) p.radix[p.nst++] = 16;
+  for (int i = 0; i < nt; ++i) p.radix[p.nst++] = tail[i];
+  for (int i = 0; i < b; ++i) p.radix[p.nst++] = 3;
+  return p;
+}
+
+// One entry of the per-axis tables (same values as build_tables).
+void table_entry(int op, int n, int i, double h, double* A, double* B) {
+  const double pi = 3.14159265358979323846;
+  auto md = [](long long a, long long m) { long long q = a % m; return q < 0 ? q + m : q; };
+  const long long kap = (i < (n + 1) / 2) ? i : i - n;
+  const double th = 2.0 * pi * (double)kap / (double)n;
+  *A = 0.0;
+  *B = 1.0;
+  switch (op) {
+    case OP_F: *A = th / h; break;
+    case OP_CD: *A = md(2 * kap, n) == 0 ? 0.0 : std::sin(th) / h; break;
+    case OP_ACD:
+      *A = md(2 * kap, n) == 0 ? 0.0 : std::sin(th) / h;
+      *B = md(4 * kap - n, 2LL * n) == 0 ? 0.0 : std::cos(th);
+      break;
+    case OP_HC: *A = md(kap, n) == 0 ? 0.0 : 2.0 * std::sin(0.5 * th) / h; break;
+    default:
+      *A = md(kap, n) == 0 ? 0.0 : 2.0 * std::sin(0.5 * th) / h;
+      *B = md(2 * kap - n, 2LL * n) == 0 ? 0.0 : std::cos(0.5 * th);
+      break;
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
 // ------------------------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -866,6 +942,154 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
   for (int k = 0; k < 5; ++k) pass_ms[k] = acc[k] / iters;
   GFP_CU(cudaGetLastError());
   return GFP_OK;
+}
+
+// Allocation-free FP64 solve (see include/gfp.h).
+int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, const double* mu,
+                      const double* ref_lambda_mu, const gfp_scheme* sc, const double E[6], double tol, int maxit,
+                      double* eps, gfp_result* out, void* cuda_stream) {
+  if (!lambda || !mu || !eps || !E || !scheme_ok(sc) || !(tol >= 0.0) || maxit < 1) return GFP_ERR_ARG;
+  if (!(h > 0.0) || !std::isfinite(h) || n1 < 1 || n2 < 1 || n3 < 1) return GFP_ERR_ARG;
+  for (int c = 0; c < 6; ++c) if (!std::isfinite(E[c])) return GFP_ERR_ARG;
+  if (sc->op == OP_DGO || sc->prec != GFP_FP64 || sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
+  if (!factor_ok(n1) || !factor_ok(n2) || !factor_ok(n3)) return GFP_ERR_UNSUPPORTED_SIZE;
+  Dims d;
+  d.n1 = n1; d.n2 = n2; d.n3 = n3;
+  d.n1h = n1 / 2 + 1;
+  d.P = ((d.n1h + 3) / 4) * 4;
+  d.N = (long long)n1 * n2 * n3;
+  d.S = (long long)n3 * n2 * d.P;
+  const LaunchCfg lc = make_cfg(d, 16);
+  const int ns[3] = {n1, n2, n3};
+  const int sblocks = 256;  // phase statistics partials
+  // scratch layout: spectrum, twiddles, tables, residual partials, state, phase statistics
+  size_t off = 0;
+  const size_t o_spec = off; off = align256(off + sizeof(double2) * 6 * (size_t)d.S);
+  size_t o_tw[3], o_A[3], o_B[3];
+  for (int r = 0; r < 3; ++r) { o_tw[r] = off; off = align256(off + sizeof(double2) * ns[r]); }
+  for (int r = 0; r < 3; ++r) { o_A[r] = off; off = align256(off + sizeof(double) * ns[r]); }
+  for (int r = 0; r < 3; ++r) { o_B[r] = off; off = align256(off + sizeof(double) * ns[r]); }
+  const size_t o_part = off; off = align256(off + sizeof(double) * (size_t)lc.z_blocks);
+  const size_t o_st = off; off = align256(off + sizeof(SolveState));
+  const size_t o_mm = off; off = align256(off + sizeof(double) * 4 * sblocks);
+  const size_t o_bad = off; off = align256(off + sizeof(unsigned long long));
+  if (off > kNoAllocScratchBytes) {
+    std::snprintf(g_detail, sizeof(g_detail),
+                  "grid %dx%dx%d needs %zu bytes of scratch; the allocation-free entry point holds %zu", n1, n2, n3,
+                  off, kNoAllocScratchBytes);
+    return GFP_ERR_UNSUPPORTED_SIZE;
+  }
+  int rc = global_setup();
+  if (rc) return rc;
+  void* base = nullptr;
+  rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  unsigned char* sb = static_cast<unsigned char*>(base);
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  double2* spec = reinterpret_cast<double2*>(sb + o_spec);
+  double* partials = reinterpret_cast<double*>(sb + o_part);
+  SolveState* st = reinterpret_cast<SolveState*>(sb + o_st);
+  double2* tw[3];
+  GammaParams<double> gp;
+  // twiddles and wave-vector tables, staged through a small host buffer
+  const double pi = 3.14159265358979323846;
+  for (int r = 0; r < 3; ++r) {
+    tw[r] = reinterpret_cast<double2*>(sb + o_tw[r]);
+    double* A = reinterpret_cast<double*>(sb + o_A[r]);
+    double* B = reinterpret_cast<double*>(sb + o_B[r]);
+    gp.A[r] = A;
+    gp.B[r] = B;
+    for (int j0 = 0; j0 < ns[r]; j0 += 64) {
+      double2 t64[64];
+      double a64[64], b64[64];
+      const int cnt = std::min(64, ns[r] - j0);
+      for (int j = 0; j < cnt; ++j) {
+        const double ang = -2.0 * pi * (double)(j0 + j) / (double)ns[r];
+        t64[j].x = std::cos(ang);
+        t64[j].y = std::sin(ang);
+        table_entry(sc->op, ns[r], j0 + j, h, &a64[j], &b64[j]);
+      }
+      GFP_CU(cudaMemcpyAsync(tw[r] + j0, t64, sizeof(double2) * cnt, cudaMemcpyHostToDevice, stream));
+      GFP_CU(cudaMemcpyAsync(A + j0, a64, sizeof(double) * cnt, cudaMemcpyHostToDevice, stream));
+      GFP_CU(cudaMemcpyAsync(B + j0, b64, sizeof(double) * cnt, cudaMemcpyHostToDevice, stream));
+      GFP_CU(cudaStreamSynchronize(stream));
+    }
+  }
+  // reference medium: given, or 1/2 (min + max) of each Lame constant; invalid moduli are rejected
+  double lam_h, mu_h;
+  {
+    double* mm = reinterpret_cast<double*>(sb + o_mm);
+    unsigned long long* bad = reinterpret_cast<unsigned long long*>(sb + o_bad);
+    GFP_CU(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), stream));
+    phase_stats_kernel<<<sblocks, 256, 0, stream>>>(lambda, mu, d.N, mm, bad);
+    GFP_CU(cudaGetLastError());
+    double mmh[4 * sblocks];
+    unsigned long long badh = 0;
+    GFP_CU(cudaMemcpyAsync(mmh, mm, sizeof(mmh), cudaMemcpyDeviceToHost, stream));
+    GFP_CU(cudaMemcpyAsync(&badh, bad, sizeof(badh), cudaMemcpyDeviceToHost, stream));
+    GFP_CU(cudaStreamSynchronize(stream));
+    if (badh) return GFP_ERR_ARG;
+    double q[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+    for (int b = 0; b < sblocks; ++b)
+      for (int j = 0; j < 4; ++j) q[j] = std::min(q[j], mmh[4 * b + j]);
+    if (ref_lambda_mu) {
+      if (!std::isfinite(ref_lambda_mu[0]) || !std::isfinite(ref_lambda_mu[1]) || !(ref_lambda_mu[1] > 0.0) ||
+          !(ref_lambda_mu[0] + 2.0 * ref_lambda_mu[1] > 0.0))
+        return GFP_ERR_ARG;
+      lam_h = ref_lambda_mu[0];
+      mu_h = ref_lambda_mu[1];
+    } else {
+      lam_h = 0.5 * (q[0] - q[1]);
+      mu_h = 0.5 * (q[2] - q[3]);
+    }
+  }
+  gp.c_mu = 1.0 / (2.0 * mu_h);
+  gp.c_lm = (lam_h + mu_h) / (mu_h * (lam_h + 2.0 * mu_h));
+  gp.invN = 1.0 / (double)d.N;
+  gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
+  FftPlan plan[3];
+  for (int r = 0; r < 3; ++r) plan[r] = make_plan_fixed(ns[r]);
+  // the shared scratch keeps the previous call's contents: clear the spectrum, reset the state
+  GFP_CU(cudaMemsetAsync(spec, 0, sizeof(double2) * 6 * (size_t)d.S, stream));
+  fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, stream>>>(eps, d.N, E[0], E[1], E[2],
+                                                                                        E[3], E[4], E[5]);
+  SolveState sh;
+  std::memset(&sh, 0, sizeof(sh));
+  sh.maxit = maxit;
+  sh.tol = tol;
+  sh.eta = INFINITY;
+  sh.eta_min = INFINITY;
+  GFP_CU(cudaMemcpyAsync(st, &sh, sizeof(SolveState), cudaMemcpyHostToDevice, stream));
+  GFP_CU(cudaStreamSynchronize(stream));
+  int launched = 0, chunk = 2;
+  while (launched < maxit) {
+    const int nb = std::min(chunk, maxit - launched);
+    for (int b = 0; b < nb; ++b) {
+      const int flags = (launched + b) > 0 ? PX_DELTA : 0;
+      Passes<double>::pass_x(stream, lc, spec, eps, lambda, mu, tw[0], plan[0], d, flags, nullptr, nullptr, st);
+      Passes<double>::pass_y(stream, lc, false, spec, tw[1], plan[1], d, st);
+      Passes<double>::pass_z(stream, lc, spec, tw[2], plan[2], d, gp, partials, st, PZ_GAMMA, nullptr);
+      launch_reduce_eta(stream, partials, lc.z_blocks, st, nullptr, 0);
+      Passes<double>::pass_y(stream, lc, true, spec, tw[1], plan[1], d, st);
+    }
+    launched += nb;
+    GFP_CU(cudaGetLastError());
+    GFP_CU(cudaMemcpyAsync(&sh, st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream));
+    GFP_CU(cudaStreamSynchronize(stream));
+    if (sh.done) break;
+    chunk = std::min(chunk * 2, 64);
+  }
+  int status = GFP_OK;
+  if (sh.done == 2 || sh.done == 0) status = GFP_ERR_NOT_CONVERGED;
+  if (sh.done == 3) status = GFP_ERR_DIVERGED;
+  if (out) {
+    out->iters = sh.it;
+    out->outer = 0;
+    out->residual = sh.eta;
+    for (int c = 0; c < 6; ++c) out->sigma_mean[c] = sh.T0[c] / (double)d.N;
+    out->status = status;
+  }
+  return status;
 }
 
 }  // extern "C"

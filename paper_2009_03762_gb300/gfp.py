@@ -44,7 +44,7 @@ _lib = None
 
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
-           "gfp_time_passes", "gfp_last_error_detail")
+           "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc")
 
 
 def lib():
@@ -69,6 +69,8 @@ def lib():
     L.gfp_time_passes.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
     L.gfp_error_string.argtypes = [ip]
     L.gfp_error_string.restype = ctypes.c_char_p
+    L.gfp_solve_noalloc.argtypes = [ip, ip, ip, dp, vp, vp, vp, ctypes.POINTER(Scheme), vp, dp, ip, vp,
+                                     ctypes.POINTER(_Result), vp]
     L.gfp_last_error_detail.argtypes = []
     L.gfp_last_error_detail.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -228,6 +230,35 @@ def solve(lam, mu, op="AFB_R", E=(0.01, 0, 0, 0, 0, 0), tol=1e-8, maxit=1000, di
         return r, g.strain()
     finally:
         g.close()
+
+
+def solve_noalloc(lam, mu, eps, sch, E, tol=1e-8, maxit=1000, h=1.0, ref=None, stream=None):
+    """Allocation-free FP64 solve through gfp_solve_noalloc.
+
+    lam, mu: CUDA float64 tensors [n3, n2, n1]; eps: CUDA float64 tensor [6, n3, n2, n1] that receives
+    the strain.  The library allocates no device memory for this call (its scratch is a fixed device
+    array inside the library), so it suits callers that must not allocate.  Returns (status, Result).
+    """
+    import torch
+    for a in (lam, mu, eps):
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+            raise ValueError("expected contiguous CUDA float64 tensors")
+    n3, n2, n1 = lam.shape
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    Ec = (ctypes.c_double * 6)(*[float(v) for v in E])
+    refp = None
+    if ref is not None:
+        refa = (ctypes.c_double * 2)(float(ref[0]), float(ref[1]))
+        refp = ctypes.cast(refa, ctypes.c_void_p)
+    r = _Result()
+    rc = lib().gfp_solve_noalloc(n1, n2, n3, float(h), ctypes.c_void_p(lam.data_ptr()),
+                                 ctypes.c_void_p(mu.data_ptr()), refp, ctypes.byref(sch),
+                                 ctypes.cast(Ec, ctypes.c_void_p), float(tol), int(maxit),
+                                 ctypes.c_void_p(eps.data_ptr()), ctypes.byref(r), ctypes.c_void_p(stream))
+    if rc not in (0, -4, -5):
+        raise GfpError(rc, "gfp_solve_noalloc")
+    return rc, Result(r, rc, None)
 
 
 def _autograd():
