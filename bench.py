@@ -113,6 +113,9 @@ def run_gfp(args):
     g.set_phases(lam_d, mu_d)
     prec = args.prec
     sch = gfp.scheme(args.op, "PCD", prec)
+    tiles = g.tune(sch) if args.tune else None
+    if args.tune and prec == "MIXED":
+        g.tune(gfp.scheme(args.op, "PCD", "FP64"))
     E = [0.0, 0.0, 0.0, 0.0, 0.0, 0.5]
     K, W = args.steps, args.warmup
     g.solve(sch, E, 0.0, W)                   # warm-up
@@ -170,7 +173,7 @@ def run_gfp(args):
         "dtype": "f32+f64" if prec == "MIXED" else "f64", "data": "synthetic",
         "config": {"workload": "random spheres %d^3, vf 0.25, r U[6,16], contrast 100, PCD %s, %s"
                    % (n, args.op, "FP32 bulk / FP64 residual+refinement" if prec == "MIXED" else "FP64"),
-                   "grid": n, "scheme": args.op, "precision": prec,
+                   "grid": n, "scheme": args.op, "precision": prec, "tiles": tiles,
                    "l2": "inputs larger than L2 (spectrum %.0f MB)" % (6 * (8 if prec == "MIXED" else 16)
                                                                       * (n // 2 + 1) * n * n / 1e6)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -197,10 +200,11 @@ def passes_only(args):
     lam, mu = workload(n)
     g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
     g.set_phases(lam, mu)
+    tiles = g.tune(gfp.scheme(args.op, "PCD", args.prec)) if args.tune else None
     ms = g.time_passes(gfp.scheme(args.op, "PCD", args.prec), args.passes_only)
     bpv = bytes_per_voxel(n, args.prec)
     names = ["pass_x", "pass_y", "pass_z_gamma", "reduce_eta", "pass_y_inv"]
-    out = {"n": n, "prec": args.prec, "pass_ms": dict(zip(names, map(float, ms)))}
+    out = {"n": n, "prec": args.prec, "tiles": tiles, "pass_ms": dict(zip(names, map(float, ms)))}
     out["gbs"] = {k: bpv[k] * n ** 3 / (out["pass_ms"][k] * 1e-3) / 1e9 for k in bpv}
     g.close()
     return out
@@ -234,6 +238,7 @@ def main():
     ap.add_argument("--prec", default="MIXED", choices=["MIXED", "FP64"])
     ap.add_argument("--ttt", type=int, default=1, help="also time full solves to eta = 1e-8 (mixed and FP64)")
     ap.add_argument("--ttt-maxit", type=int, default=3000)
+    ap.add_argument("--tune", type=int, default=1, help="run the tile autotuner before timing")
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--passes-only", type=int, default=0,

@@ -239,7 +239,17 @@ LaunchCfg make_cfg(const Dims& d, int eb) {
   c.z_cols = std::max(1, std::min(zc, d.n1h));
   c.z_threads = clampt(6 * c.z_cols * d.n3 / 8);
   c.z_blocks = ((d.n1h + c.z_cols - 1) / c.z_cols) * d.n2;
+  c.cx_lines = 0;
   return c;
+}
+
+// Recompute the thread counts and partial-sum count after a tile change.
+void finalize_cfg(const Dims& d, LaunchCfg& c) {
+  auto clampt = [](int t) { return std::min(512, std::max(64, round32(t))); };
+  c.x_threads = clampt(3 * c.x_lines * d.n1 / 8);
+  c.y_threads = clampt(c.y_cols * d.n2 / 8);
+  c.z_threads = clampt(6 * c.z_cols * d.n3 / 8);
+  c.z_blocks = ((d.n1h + c.z_cols - 1) / c.z_cols) * d.n2;
 }
 
 // Per-axis tables with exact zeros (kappa from the storage index; Nyquist is kappa = -n/2)
@@ -705,7 +715,7 @@ int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_gri
     A((void**)&g->tabA[r], sizeof(double) * ns[r]);
     A((void**)&g->tabB[r], sizeof(double) * ns[r]);
   }
-  g->np_max = g->lc64.z_blocks;
+  g->np_max = d.n1h * d.n2;  // enough for any z-tile width (one column per CTA)
   A((void**)&g->partials, sizeof(double) * g->np_max);
   A((void**)&g->st, sizeof(SolveState));
   A((void**)&g->scratch, sizeof(double) * 4 * 1024);
@@ -1090,6 +1100,130 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
     out->status = status;
   }
   return status;
+}
+
+// Autotuner: time candidate tile shapes of each pass (register-FFT x-pass lines, y and z tile
+// widths) on this grid and keep the fastest; tiles_out receives {x lines, y columns, z columns}.
+int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
+  if (!g || !scheme_ok(sc) || iters < 1 || !g->phases) return GFP_ERR_ARG;
+  if (sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
+  const bool mixed = sc->prec == GFP_MIXED;
+  if (mixed && (sc->op == OP_F || sc->op == OP_HC)) return GFP_ERR_UNSUPPORTED;
+  double dummy[5];
+  int rc = gfp_time_passes(g, sc, 1, dummy);  // prepares state, tables and (mixed) the inner source
+  if (rc) return rc;
+  const Dims& d = g->d;
+  const GammaParams<double> gp = gamma_params<double>(g, sc->op, g->tabA, g->tabB);
+  GammaParams<float> gp32;
+  if (mixed) gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
+  float2* spec32 = reinterpret_cast<float2*>(g->spec);
+  LaunchCfg& lc = mixed ? g->lc32 : g->lc64;
+  const int eb = mixed ? 8 : 16;
+  const long long budget = 200 * 1024;
+  cudaEvent_t e0, e1;
+  GFP_CU(cudaEventCreate(&e0));
+  GFP_CU(cudaEventCreate(&e1));
+  auto run = [&](int pass, const LaunchCfg& c) -> float {
+    cudaEventRecord(e0, g->stream);
+    for (int i = 0; i < iters; ++i) {
+      if (pass == 0) {
+        if (mixed)
+          Passes<float>::pass_x(g->stream, c, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, PX_DELTA,
+                                nullptr, nullptr, g->st_in);
+        else
+          Passes<double>::pass_x(g->stream, c, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_DELTA,
+                                 nullptr, nullptr, g->st);
+      } else if (pass == 1) {
+        if (mixed) Passes<float>::pass_y(g->stream, c, false, spec32, g->tw32[1], g->plan[1], d, g->st_in);
+        else Passes<double>::pass_y(g->stream, c, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+      } else {
+        if (mixed)
+          Passes<float>::pass_z(g->stream, c, spec32, g->tw32[2], g->plan[2], d, gp32, g->partials, g->st_in,
+                                PZ_INNER, g->vsrc);
+        else
+          Passes<double>::pass_z(g->stream, c, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+                                 nullptr);
+      }
+    }
+    cudaEventRecord(e1, g->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+  };
+  const int ycmax = mixed ? cy_cols_max<float>(d.n2) : cy_cols_max<double>(d.n2);
+  const int zcmax = mixed ? cz_cols_max<float>(d.n3) : cz_cols_max<double>(d.n3);
+  // x-pass lines (register-FFT sizes only)
+  {
+    const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+    LaunchCfg best = lc;
+    float bt = run(0, lc);
+    for (int L : cands) {
+      LaunchCfg c = lc;
+      c.cx_lines = L;
+      const float t = run(0, c);
+      if (t < bt) { bt = t; best = c; }
+    }
+    lc = best;
+  }
+  {
+    const int cands[] = {2, 4, 8, 16, 32};
+    LaunchCfg best = lc;
+    float bt = run(1, lc);
+    for (int cc : cands) {
+      if (cc > ycmax || cc > d.n1h || (long long)(d.n2 + 2 * cc * d.n2) * eb > budget) continue;
+      LaunchCfg c = lc;
+      c.y_cols = cc;
+      finalize_cfg(d, c);
+      const float t = run(1, c);
+      if (t < bt) { bt = t; best = c; }
+    }
+    lc = best;
+  }
+  {
+    const int cands[] = {1, 2, 4, 8, 16};
+    LaunchCfg best = lc;
+    float bt = run(2, lc);
+    for (int cc : cands) {
+      if (cc > zcmax || cc > d.n1h || (long long)(d.n3 + 12 * cc * d.n3) * eb > budget) continue;
+      LaunchCfg c = lc;
+      c.z_cols = cc;
+      finalize_cfg(d, c);
+      const float t = run(2, c);
+      if (t < bt) { bt = t; best = c; }
+    }
+    lc = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (tiles_out) { tiles_out[0] = lc.cx_lines; tiles_out[1] = lc.y_cols; tiles_out[2] = lc.z_cols; }
+  GFP_CU(cudaGetLastError());
+  return GFP_OK;
+}
+
+// Apply tile shapes (e.g. from a tuning cache): {x lines (0 = default), y columns, z columns}.
+int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
+  if (!g || !tiles || (prec != GFP_FP64 && prec != GFP_MIXED)) return GFP_ERR_ARG;
+  if (prec == GFP_MIXED) {
+    int rc = ensure_mixed(g);
+    if (rc) return rc;
+  }
+  const Dims& d = g->d;
+  const bool mixed = prec == GFP_MIXED;
+  const int eb = mixed ? 8 : 16;
+  const long long budget = 200 * 1024;
+  const int ycmax = mixed ? cy_cols_max<float>(d.n2) : cy_cols_max<double>(d.n2);
+  const int zcmax = mixed ? cz_cols_max<float>(d.n3) : cz_cols_max<double>(d.n3);
+  if (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 1 || tiles[1] > ycmax || tiles[1] > d.n1h || tiles[2] < 1 ||
+      tiles[2] > zcmax || tiles[2] > d.n1h || (long long)(d.n2 + 2 * tiles[1] * d.n2) * eb > budget ||
+      (long long)(d.n3 + 12 * tiles[2] * d.n3) * eb > budget)
+    return GFP_ERR_ARG;
+  LaunchCfg& lc = mixed ? g->lc32 : g->lc64;
+  lc.cx_lines = tiles[0];
+  lc.y_cols = tiles[1];
+  lc.z_cols = tiles[2];
+  finalize_cfg(d, lc);
+  return GFP_OK;
 }
 
 }  // extern "C"

@@ -143,8 +143,14 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
 // pass_z_gamma: CTA = C columns x 6 components x all n3 rows at fixed k2; line = (comp, col).
 // Same modes as the generic kernel (PZ_GAMMA, PZ_RESIDUAL, PZ_INNER).
 // ------------------------------------------------------------------------------------------------
+// FP32 register FFTs of up to 16 elements per thread fit two 384-thread CTAs per SM.
+template <typename R, int N> struct ZBound {
+  static constexpr int threads = (sizeof(R) == 4 && CPlan<N>::E <= 16) ? 384 : 512;
+  static constexpr int blocks = (sizeof(R) == 4 && CPlan<N>::E <= 16) ? 2 : 1;
+};
+
 template <typename R, int N>
-__global__ void __launch_bounds__(512) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
+__global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
                                                        const typename C<R>::T* __restrict__ tw, Dims d, int cols,
                                                        GammaParams<R> gp, double* __restrict__ partials,
                                                        SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {

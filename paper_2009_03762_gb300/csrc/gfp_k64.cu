@@ -2,4 +2,6 @@
 #include "gfp_kimpl.cuh"
 namespace gfp {
 template struct Passes<double>;
+template int cz_cols_max<double>(int);
+template int cy_cols_max<double>(int);
 }

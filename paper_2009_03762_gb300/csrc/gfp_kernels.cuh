@@ -372,10 +372,11 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
 // Launch configuration and host-side launchers (instantiated per precision in gfp_k64.cu / gfp_k32.cu)
 // --------------------------------------------------------------------------------------------
 struct LaunchCfg {
-  int x_lines, x_threads;
+  int x_lines, x_threads;   // generic x-pass
   int y_cols, y_threads;
   int z_cols, z_threads;
-  int z_blocks;  // number of pass_z CTAs (partials written)
+  int z_blocks;             // number of pass_z CTAs (partials written)
+  int cx_lines;             // lines per CTA of the register-FFT x-pass (0: default)
 };
 
 template <typename R>
@@ -392,5 +393,8 @@ struct Passes {
 };
 
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap);
+
+template <typename R> int cz_cols_max(int n3);
+template <typename R> int cy_cols_max(int n2);
 
 }  // namespace gfp

@@ -26,14 +26,14 @@ cudaError_t Passes<R>::setup() {
 }
 
 // lines per CTA of the compile-time x-pass: at most 512 threads (3 pair-lines x T each)
-template <int N> inline int cx_lines() { return std::max(1, std::min(16, 512 / (3 * CPlan<N>::T))); }
+template <int N> inline int cx_lines_max() { return std::max(1, std::min(16, 512 / (3 * CPlan<N>::T))); }
 
 template <typename R, int N>
-inline void launch_x_c(cudaStream_t s, typename C<R>::T* spec, R* eps, const R* lam, const R* mu,
+inline void launch_x_c(cudaStream_t s, int want_lines, typename C<R>::T* spec, R* eps, const R* lam, const R* mu,
                        const typename C<R>::T* tw, const Dims& d, int flags, const float* corr, const double* corr_mean,
                        const SolveState* st) {
   typedef typename C<R>::T T;
-  const int lines = cx_lines<N>();
+  const int lines = want_lines > 0 ? std::min(want_lines, cx_lines_max<N>()) : cx_lines_max<N>();
   const long long nlines = (long long)d.n2 * d.n3;
   const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
   const size_t sm = sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16));
@@ -47,7 +47,7 @@ void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, con
                        const SolveState* st) {
   switch (d.n1) {
 #define GFP_CASE(N) \
-    case N: launch_x_c<R, N>(s, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, st); return;
+    case N: launch_x_c<R, N>(s, lc.cx_lines, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, st); return;
     GFP_FOR_CSIZES(GFP_CASE)
 #undef GFP_CASE
     default: break;
@@ -101,4 +101,26 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
   pass_z_gamma_kernel<R><<<grid, lc.z_threads, sm, s>>>(spec, tw, plan, d, lc.z_cols, gp, partials, st, mode, vsrc);
 }
 
+}  // namespace gfp
+
+namespace gfp {
+// Largest z-tile width (k1 columns) the register-FFT z-pass accepts for this length and precision.
+template <typename R> int cz_cols_max(int n3) {
+  switch (n3) {
+#define GFP_CASE(N) \
+    case N: return std::max(1, ZBound<R, N>::threads / (6 * CPlan<N>::T));
+    GFP_FOR_CSIZES(GFP_CASE)
+#undef GFP_CASE
+    default: return 64;
+  }
+}
+template <typename R> int cy_cols_max(int n2) {
+  switch (n2) {
+#define GFP_CASE(N) \
+    case N: return std::max(1, 512 / CPlan<N>::T);
+    GFP_FOR_CSIZES(GFP_CASE)
+#undef GFP_CASE
+    default: return 64;
+  }
+}
 }  // namespace gfp

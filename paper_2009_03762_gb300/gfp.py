@@ -44,7 +44,7 @@ _lib = None
 
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
-           "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc")
+           "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles")
 
 
 def lib():
@@ -71,6 +71,8 @@ def lib():
     L.gfp_error_string.restype = ctypes.c_char_p
     L.gfp_solve_noalloc.argtypes = [ip, ip, ip, dp, vp, vp, vp, ctypes.POINTER(Scheme), vp, dp, ip, vp,
                                      ctypes.POINTER(_Result), vp]
+    L.gfp_tune.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
+    L.gfp_set_tiles.argtypes = [vp, ip, vp]
     L.gfp_last_error_detail.argtypes = []
     L.gfp_last_error_detail.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -84,6 +86,14 @@ def _check(rc, where, ok=(0,)):
     if rc not in ok:
         raise GfpError(rc, where)
     return rc
+
+
+def _gpu_name():
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "gpu"
 
 
 def scheme(op="AFB_R", disc="TD", prec="FP64", dgo_m=0, stop_rule=0):
@@ -207,6 +217,39 @@ class Grid:
         _check(lib().gfp_time_passes(self._h, ctypes.byref(sch), int(iters), ms.ctypes.data_as(ctypes.c_void_p)),
                "gfp_time_passes")
         return ms
+
+    def tune(self, sch, iters=5, cache=None):
+        """Choose tile shapes with the native autotuner, or reuse them from a JSON cache.
+
+        cache: path of a JSON file (default: $GFP_TUNE_CACHE if set); entries are keyed by grid size,
+        precision and GPU name.
+        """
+        import json
+        prec = sch.prec
+        path = cache or os.environ.get("GFP_TUNE_CACHE")
+        key = "%dx%dx%d:%d:%s" % (self.shape[2], self.shape[1], self.shape[0], prec, _gpu_name())
+        table = {}
+        if path and os.path.exists(path):
+            try:
+                with open(path) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+        if key in table:
+            tiles = (ctypes.c_int * 3)(*table[key])
+            _check(lib().gfp_set_tiles(self._h, int(prec), ctypes.cast(tiles, ctypes.c_void_p)), "gfp_set_tiles")
+            return list(table[key])
+        out = (ctypes.c_int * 3)()
+        _check(lib().gfp_tune(self._h, ctypes.byref(sch), int(iters), ctypes.cast(out, ctypes.c_void_p)), "gfp_tune")
+        if path:
+            table[key] = list(out)
+            with open(path, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return list(out)
+
+    def set_tiles(self, prec, tiles):
+        t = (ctypes.c_int * 3)(*[int(v) for v in tiles])
+        _check(lib().gfp_set_tiles(self._h, int(prec), ctypes.cast(t, ctypes.c_void_p)), "gfp_set_tiles")
 
     def get_state(self):
         eps = np.empty((6,) + self.shape)

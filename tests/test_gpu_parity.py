@@ -196,3 +196,24 @@ def test_parity_register_fft_sizes(gfp, shape, op):
     ref = O.solve(lam, mu, op, E, max_iters_exact=3)
     assert _rel(eps, ref.eps) <= REL
     assert _rel(r.sigma_mean, ref.sigma_mean) <= REL
+
+
+@pytest.mark.parametrize("prec,op", [("FP64", "F"), ("MIXED", "AFB_R")])
+def test_autotuned_tiles_keep_parity(gfp, prec, op, tmp_path):
+    """The tile autotuner changes launch shapes only: results stay at oracle parity; the cache is reused."""
+    lam, mu = M.random_spheres(32, vf=0.2, rmin=3.0, rmax=5.0, contrast=20.0, seed=4)
+    g = gfp.Grid(32, 32, 32)
+    g.set_phases(lam, mu)
+    sch = gfp.scheme(op, "PCD", prec)
+    cache = str(tmp_path / "tiles.json")
+    tiles = g.tune(sch, iters=2, cache=cache)
+    assert len(tiles) == 3 and g.tune(sch, cache=cache) == tiles
+    E = [0.0, 0.0, 0.0, 0.0, 0.0, 0.5]
+    if prec == "FP64":
+        r = g.solve(sch, E, 0.0, 5)
+        ref = O.solve(lam, mu, op, E, max_iters_exact=5, disc="PCD")
+        assert _rel(g.strain(), ref.eps) <= REL
+    else:
+        r = g.solve(sch, E, 1e-8, 5000)
+        ref = O.solve(lam, mu, op, E, tol=1e-9, maxit=5000, disc="PCD")
+        assert r.converged and _rel(r.sigma_mean, ref.sigma_mean) <= 1e-6
