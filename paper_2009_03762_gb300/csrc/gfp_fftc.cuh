@@ -23,7 +23,7 @@ GFP_CPLAN(96, 24, 3, 8, 4, 3)
 GFP_CPLAN(128, 16, 2, 16, 8, 1)
 GFP_CPLAN(192, 24, 3, 8, 8, 3)
 GFP_CPLAN(256, 16, 2, 16, 16, 1)
-GFP_CPLAN(512, 16, 3, 16, 16, 2)
+GFP_CPLAN(512, 32, 3, 16, 16, 2)
 #undef GFP_CPLAN
 
 // Element index read by input r of butterfly b at stage S (thread position t): j + r N / R, j = t + b T.
