@@ -1,5 +1,7 @@
 // C ABI of the GFP solver: grid handles, phases, the iteration driver, effective stiffness,
 // sensitivities and checkpoint/resume.  See include/gfp.h for the contract of each call.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -185,7 +187,9 @@ struct gfp_grid_s {
   double* cpart = nullptr;     // its per-block partials
   bool mixed_ready = false;
   bool lam32_valid = false;
+  CUtensorMap zmap64, zmap32;  // TMA descriptors of the z-tiles for lc64 / lc32
 };
+
 
 namespace {
 
@@ -240,7 +244,48 @@ LaunchCfg make_cfg(const Dims& d, int eb) {
   c.z_threads = clampt(6 * c.z_cols * d.n3 / 8);
   c.z_blocks = ((d.n1h + c.z_cols - 1) / c.z_cols) * d.n2;
   c.cx_lines = 0;
+  c.ztmap = nullptr;
   return c;
+}
+
+// cuTensorMapEncodeTiled from the driver (looked up once; null if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a half spectrum (FP32 or FP64 complex) as reals {2P, n2, n3, 6} with z-tiles of
+// `cols` columns x min(n3, 256) rows.  Returns false if the shape is not TMA-eligible.
+bool encode_ztmap(CUtensorMap* m, const void* spec, const Dims& d, int cols, int real_bytes) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || cols < 1 || (2 * cols * real_bytes) % 16 != 0 || ((uintptr_t)spec & 15) != 0) return false;
+  const cuuint64_t es = (cuuint64_t)real_bytes;
+  cuuint64_t dims[4] = {(cuuint64_t)(2 * d.P), (cuuint64_t)d.n2, (cuuint64_t)d.n3, 6};
+  cuuint64_t strides[3] = {2 * (cuuint64_t)d.P * es, (cuuint64_t)d.n2 * 2 * d.P * es, (cuuint64_t)d.S * 2 * es};
+  cuuint32_t box[4] = {(cuuint32_t)(2 * cols), 1, (cuuint32_t)std::min(d.n3, 256), 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, real_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                         const_cast<void*>(spec), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// (Re)encode the z-tile tensor map of a launch configuration; without TMA the pass falls back to
+// the register-FFT kernel with ordinary loads.
+void refresh_ztmap(gfp_grid g, bool mixed) {
+  LaunchCfg& lc = mixed ? g->lc32 : g->lc64;
+  CUtensorMap* m = mixed ? &g->zmap32 : &g->zmap64;
+  lc.ztmap = encode_ztmap(m, g->spec, g->d, lc.z_cols, mixed ? 4 : 8) ? m : nullptr;
 }
 
 // Recompute the thread counts and partial-sum count after a tile change.
@@ -431,6 +476,7 @@ int ensure_mixed(gfp_grid g) {
   const Dims& d = g->d;
   const int ns[3] = {g->n1, g->n2, g->n3};
   g->lc32 = make_cfg(d, 8);
+  refresh_ztmap(g, true);
   GFP_CU(cudaMalloc(&g->lam32, sizeof(float) * d.N));
   GFP_CU(cudaMalloc(&g->mu32, sizeof(float) * d.N));
   GFP_CU(cudaMalloc(&g->eps32, sizeof(float) * 6 * d.N));
@@ -737,6 +783,7 @@ int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_gri
   e = cudaMemsetAsync(g->spec, 0, sizeof(double2) * 6 * d.S, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) { free_grid(g); return cuda_status(e); }
+  refresh_ztmap(g, false);
   *out = g;
   return GFP_OK;
 }
@@ -1184,15 +1231,18 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     const int cands[] = {1, 2, 4, 8, 16};
     LaunchCfg best = lc;
     float bt = run(2, lc);
+    CUtensorMap cand_map;
     for (int cc : cands) {
       if (cc > zcmax || cc > d.n1h || (long long)(d.n3 + 12 * cc * d.n3) * eb > budget) continue;
       LaunchCfg c = lc;
       c.z_cols = cc;
       finalize_cfg(d, c);
+      c.ztmap = encode_ztmap(&cand_map, g->spec, d, cc, mixed ? 4 : 8) ? &cand_map : nullptr;
       const float t = run(2, c);
       if (t < bt) { bt = t; best = c; }
     }
     lc = best;
+    refresh_ztmap(g, mixed);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1223,6 +1273,7 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   lc.y_cols = tiles[1];
   lc.z_cols = tiles[2];
   finalize_cfg(d, lc);
+  refresh_ztmap(g, mixed);
   return GFP_OK;
 }
 

@@ -377,6 +377,7 @@ struct LaunchCfg {
   int z_cols, z_threads;
   int z_blocks;             // number of pass_z CTAs (partials written)
   int cx_lines;             // lines per CTA of the register-FFT x-pass (0: default)
+  const void* ztmap;        // host CUtensorMap of the spectrum for TMA z-tiles of z_cols columns, or null
 };
 
 template <typename R>

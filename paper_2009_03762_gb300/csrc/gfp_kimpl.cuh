@@ -2,7 +2,7 @@
 // Grid sizes with a compile-time FFT plan (CPlan) use the register-resident kernels of
 // gfp_fftc.cuh; every other 2^a 3^b size uses the generic shared-memory Stockham kernels.
 #pragma once
-#include "gfp_fftc.cuh"
+#include "gfp_tma.cuh"
 
 namespace gfp {
 
@@ -22,7 +22,32 @@ cudaError_t Passes<R>::setup() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   GFP_FOR_CSIZES(GFP_SET)
 #undef GFP_SET
+#define GFP_SET_TMA(N) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_tma_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  GFP_FOR_CSIZES(GFP_SET_TMA)
+#undef GFP_SET_TMA
   return e;
+}
+
+// Persistent-grid size of the TMA z-pass: resident CTAs per SM x SMs (cached per configuration).
+template <typename R, int N>
+inline int tma_grid(int threads, size_t smem) {
+  static int sms = 0;
+  static int cached_threads = -1, cached_blocks = 0;
+  static size_t cached_smem = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (threads != cached_threads || smem != cached_smem) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_z_tma_kernel<R, N>, threads, smem);
+    cached_threads = threads;
+    cached_smem = smem;
+    cached_blocks = nb > 0 ? nb : 1;
+  }
+  return sms * cached_blocks;
 }
 
 // lines per CTA of the compile-time x-pass: at most 512 threads (3 pair-lines x T each)
@@ -84,12 +109,21 @@ void Passes<R>::pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spe
 template <typename R>
 void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw, const FftPlan& plan, const Dims& d,
                        const GammaParams<R>& gp, double* partials, SolveState* st, int mode, float2* vsrc) {
-  dim3 grid((d.n1h + lc.z_cols - 1) / lc.z_cols, d.n2, 1);
+  const int ntx = (d.n1h + lc.z_cols - 1) / lc.z_cols;
+  dim3 grid(ntx, d.n2, 1);
   switch (d.n3) {
 #define GFP_CASE(N)                                                                                           \
     case N: {                                                                                                 \
-      const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols);                                        \
       const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
+      const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols);                                       \
+      if (lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 && smt <= 220 * 1024) {                    \
+        const int ntiles = ntx * d.n2;                                                                        \
+        const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \
+        pass_z_tma_kernel<R, N><<<gsz, th, smt, s>>>(*reinterpret_cast<const CUtensorMap*>(lc.ztmap), spec, tw, \
+                                                      d, lc.z_cols, ntx, gp, partials, st, mode, vsrc);       \
+        return;                                                                                               \
+      }                                                                                                       \
+      const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols);                                        \
       pass_z_c_kernel<R, N><<<grid, th, smc, s>>>(spec, tw, d, lc.z_cols, gp, partials, st, mode, vsrc);      \
       return;                                                                                                 \
     }
