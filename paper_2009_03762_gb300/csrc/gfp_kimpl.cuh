@@ -50,15 +50,20 @@ inline int tma_grid(int threads, size_t smem) {
   return sms * cached_blocks;
 }
 
-// lines per CTA of the compile-time x-pass: at most 512 threads (3 pair-lines x T each)
-template <int N> inline int cx_lines_max() { return std::max(1, std::min(16, 512 / (3 * CPlan<N>::T))); }
+// lines per CTA of the compile-time x-pass: at most 512 threads (3 pair-lines x T each) and at most
+// 200 KB of shared memory (3 padded lines of N + N/16 elements per x-line, plus N twiddles)
+template <typename R, int N> inline int cx_lines_max() {
+  const int by_threads = 512 / (3 * CPlan<N>::T);
+  const int by_smem = (int)((200 * 1024 / sizeof(typename C<R>::T) - N) / (3 * (N + N / 16)));
+  return std::max(1, std::min(16, std::min(by_threads, by_smem)));
+}
 
 template <typename R, int N>
 inline void launch_x_c(cudaStream_t s, int want_lines, typename C<R>::T* spec, R* eps, const R* lam, const R* mu,
                        const typename C<R>::T* tw, const Dims& d, int flags, const float* corr, const double* corr_mean,
                        const SolveState* st) {
   typedef typename C<R>::T T;
-  const int lines = want_lines > 0 ? std::min(want_lines, cx_lines_max<N>()) : cx_lines_max<N>();
+  const int lines = want_lines > 0 ? std::min(want_lines, cx_lines_max<R, N>()) : cx_lines_max<R, N>();
   const long long nlines = (long long)d.n2 * d.n3;
   const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
   const size_t sm = sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16));
