@@ -131,12 +131,13 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* scheme, int iters, double pass
 
 /* Autotuner (no counterpart in the paper): times candidate tile shapes of each pass on this grid for
  * the scheme's precision -- lines per CTA of the register-FFT x-pass, k1 columns per CTA of the y and
- * z passes -- and keeps the fastest.  tiles_out (may be NULL) receives {x lines, y columns, z columns}.
+ * z passes, and whether the z-pass loads its tiles with TMA -- and keeps the fastest.  tiles_out (may be
+ * NULL) receives {x lines, y columns, z columns}, the z entry negated when the TMA z-pass is chosen.
  * The strain state is modified; call before a solve. */
 int gfp_tune(gfp_grid g, const gfp_scheme* scheme, int iters, int tiles_out[3]);
 
-/* Apply tile shapes for one precision (GFP_FP64 or GFP_MIXED), e.g. read from a tuning cache;
- * invalid shapes return GFP_ERR_ARG. */
+/* Apply tile shapes for one precision (GFP_FP64 or GFP_MIXED), e.g. read from a tuning cache, in the
+ * format gfp_tune returns; invalid shapes return GFP_ERR_ARG. */
 int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]);
 
 int gfp_destroy_grid(gfp_grid g);

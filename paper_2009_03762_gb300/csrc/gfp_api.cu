@@ -245,6 +245,7 @@ LaunchCfg make_cfg(const Dims& d, int eb) {
   c.z_blocks = ((d.n1h + c.z_cols - 1) / c.z_cols) * d.n2;
   c.cx_lines = 0;
   c.ztmap = nullptr;
+  c.z_tma = 0;
   return c;
 }
 
@@ -1234,19 +1235,23 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     CUtensorMap cand_map;
     for (int cc : cands) {
       if (cc > zcmax || cc > d.n1h || (long long)(d.n3 + 12 * cc * d.n3) * eb > budget) continue;
-      LaunchCfg c = lc;
-      c.z_cols = cc;
-      finalize_cfg(d, c);
-      c.ztmap = encode_ztmap(&cand_map, g->spec, d, cc, mixed ? 4 : 8) ? &cand_map : nullptr;
-      const float t = run(2, c);
-      if (t < bt) { bt = t; best = c; }
+      for (int use_tma = 0; use_tma < 2; ++use_tma) {
+        LaunchCfg c = lc;
+        c.z_cols = cc;
+        c.z_tma = use_tma;
+        finalize_cfg(d, c);
+        c.ztmap = (use_tma && encode_ztmap(&cand_map, g->spec, d, cc, mixed ? 4 : 8)) ? &cand_map : nullptr;
+        if (use_tma && !c.ztmap) continue;
+        const float t = run(2, c);
+        if (t < bt) { bt = t; best = c; }
+      }
     }
     lc = best;
     refresh_ztmap(g, mixed);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (tiles_out) { tiles_out[0] = lc.cx_lines; tiles_out[1] = lc.y_cols; tiles_out[2] = lc.z_cols; }
+  if (tiles_out) { tiles_out[0] = lc.cx_lines; tiles_out[1] = lc.y_cols; tiles_out[2] = lc.z_tma ? -lc.z_cols : lc.z_cols; }
   GFP_CU(cudaGetLastError());
   return GFP_OK;
 }
@@ -1264,14 +1269,16 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   const long long budget = 200 * 1024;
   const int ycmax = mixed ? cy_cols_max<float>(d.n2) : cy_cols_max<double>(d.n2);
   const int zcmax = mixed ? cz_cols_max<float>(d.n3) : cz_cols_max<double>(d.n3);
-  if (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 1 || tiles[1] > ycmax || tiles[1] > d.n1h || tiles[2] < 1 ||
-      tiles[2] > zcmax || tiles[2] > d.n1h || (long long)(d.n2 + 2 * tiles[1] * d.n2) * eb > budget ||
-      (long long)(d.n3 + 12 * tiles[2] * d.n3) * eb > budget)
+  const int zc = tiles[2] < 0 ? -tiles[2] : tiles[2];
+  if (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 1 || tiles[1] > ycmax || tiles[1] > d.n1h || zc < 1 ||
+      zc > zcmax || zc > d.n1h || (long long)(d.n2 + 2 * tiles[1] * d.n2) * eb > budget ||
+      (long long)(d.n3 + 12 * zc * d.n3) * eb > budget)
     return GFP_ERR_ARG;
   LaunchCfg& lc = mixed ? g->lc32 : g->lc64;
   lc.cx_lines = tiles[0];
   lc.y_cols = tiles[1];
-  lc.z_cols = tiles[2];
+  lc.z_cols = zc;
+  lc.z_tma = tiles[2] < 0 ? 1 : 0;
   finalize_cfg(d, lc);
   refresh_ztmap(g, mixed);
   return GFP_OK;

@@ -378,6 +378,7 @@ struct LaunchCfg {
   int z_blocks;             // number of pass_z CTAs (partials written)
   int cx_lines;             // lines per CTA of the register-FFT x-pass (0: default)
   const void* ztmap;        // host CUtensorMap of the spectrum for TMA z-tiles of z_cols columns, or null
+  int z_tma;                // use the TMA-fed z-pass when eligible (1) or the register-FFT one (0)
 };
 
 template <typename R>

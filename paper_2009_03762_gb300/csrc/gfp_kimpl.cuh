@@ -121,7 +121,7 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
     case N: {                                                                                                 \
       const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
       const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols);                                       \
-      if (lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 && smt <= 220 * 1024) {                    \
+      if (lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 && smt <= 220 * 1024) {                    \
         const int ntiles = ntx * d.n2;                                                                        \
         const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \
         pass_z_tma_kernel<R, N><<<gsz, th, smt, s>>>(*reinterpret_cast<const CUtensorMap*>(lc.ztmap), spec, tw, \

@@ -61,7 +61,7 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 // Tensor map of the half spectrum seen as a 4D array of reals: {2 P (re/im interleaved), n2, n3, 6};
 // the box is {2 C, 1, min(n3, 256), 1}, so one load brings C columns x up to 256 rows of one component.
 template <typename R, int N>
-__global__ void __launch_bounds__(384, 1) pass_z_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                             typename C<R>::T* __restrict__ spec,
                                                             const typename C<R>::T* __restrict__ tw, Dims d, int cols,
                                                             int ntx, GammaParams<R> gp, double* __restrict__ partials,
