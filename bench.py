@@ -200,7 +200,11 @@ def passes_only(args):
     lam, mu = workload(n)
     g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
     g.set_phases(lam, mu)
-    tiles = g.tune(gfp.scheme(args.op, "PCD", args.prec)) if args.tune else None
+    if args.tiles:
+        tiles = [int(v) for v in args.tiles.split(",")]
+        g.set_tiles(gfp.MIXED if args.prec == "MIXED" else gfp.FP64, tiles)
+    else:
+        tiles = g.tune(gfp.scheme(args.op, "PCD", args.prec)) if args.tune else None
     ms = g.time_passes(gfp.scheme(args.op, "PCD", args.prec), args.passes_only)
     bpv = bytes_per_voxel(n, args.prec)
     names = ["pass_x", "pass_y", "pass_z_gamma", "reduce_eta", "pass_y_inv"]
@@ -239,6 +243,7 @@ def main():
     ap.add_argument("--ttt", type=int, default=1, help="also time full solves to eta = 1e-8 (mixed and FP64)")
     ap.add_argument("--ttt-maxit", type=int, default=3000)
     ap.add_argument("--tune", type=int, default=1, help="run the tile autotuner before timing")
+    ap.add_argument("--tiles", default="", help="x lines,y columns,z columns (negative z: TMA z-pass)")
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--passes-only", type=int, default=0,

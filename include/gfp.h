@@ -132,7 +132,8 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* scheme, int iters, double pass
 /* Autotuner (no counterpart in the paper): times candidate tile shapes of each pass on this grid for
  * the scheme's precision -- lines per CTA of the register-FFT x-pass, k1 columns per CTA of the y and
  * z passes, and whether the z-pass loads its tiles with TMA -- and keeps the fastest.  tiles_out (may be
- * NULL) receives {x lines, y columns, z columns}, the z entry negated when the TMA z-pass is chosen.
+ * NULL) receives {x lines, y columns, z columns}, the x entry negated when the x-pass stages its loads
+ * with cp.async and the z entry negated when the TMA z-pass is chosen.
  * The strain state is modified; call before a solve. */
 int gfp_tune(gfp_grid g, const gfp_scheme* scheme, int iters, int tiles_out[3]);
 

@@ -246,6 +246,7 @@ LaunchCfg make_cfg(const Dims& d, int eb) {
   c.cx_lines = 0;
   c.ztmap = nullptr;
   c.z_tma = 0;
+  c.x_async = 0;
   return c;
 }
 
@@ -1207,10 +1208,13 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     LaunchCfg best = lc;
     float bt = run(0, lc);
     for (int L : cands) {
-      LaunchCfg c = lc;
-      c.cx_lines = L;
-      const float t = run(0, c);
-      if (t < bt) { bt = t; best = c; }
+      for (int xa = 0; xa < 2; ++xa) {
+        LaunchCfg c = lc;
+        c.cx_lines = L;
+        c.x_async = xa;
+        const float t = run(0, c);
+        if (t < bt) { bt = t; best = c; }
+      }
     }
     lc = best;
   }
@@ -1251,7 +1255,11 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (tiles_out) { tiles_out[0] = lc.cx_lines; tiles_out[1] = lc.y_cols; tiles_out[2] = lc.z_tma ? -lc.z_cols : lc.z_cols; }
+  if (tiles_out) {
+    tiles_out[0] = lc.x_async ? -lc.cx_lines : lc.cx_lines;
+    tiles_out[1] = lc.y_cols;
+    tiles_out[2] = lc.z_tma ? -lc.z_cols : lc.z_cols;
+  }
   GFP_CU(cudaGetLastError());
   return GFP_OK;
 }
@@ -1270,12 +1278,14 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   const int ycmax = mixed ? cy_cols_max<float>(d.n2) : cy_cols_max<double>(d.n2);
   const int zcmax = mixed ? cz_cols_max<float>(d.n3) : cz_cols_max<double>(d.n3);
   const int zc = tiles[2] < 0 ? -tiles[2] : tiles[2];
-  if (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 1 || tiles[1] > ycmax || tiles[1] > d.n1h || zc < 1 ||
+  const int xl = tiles[0] < 0 ? -tiles[0] : tiles[0];
+  if (xl > 16 || tiles[1] < 1 || tiles[1] > ycmax || tiles[1] > d.n1h || zc < 1 ||
       zc > zcmax || zc > d.n1h || (long long)(d.n2 + 2 * tiles[1] * d.n2) * eb > budget ||
       (long long)(d.n3 + 12 * zc * d.n3) * eb > budget)
     return GFP_ERR_ARG;
   LaunchCfg& lc = mixed ? g->lc32 : g->lc64;
-  lc.cx_lines = tiles[0];
+  lc.cx_lines = xl;
+  lc.x_async = tiles[0] < 0 ? 1 : 0;
   lc.y_cols = tiles[1];
   lc.z_cols = zc;
   lc.z_tma = tiles[2] < 0 ? 1 : 0;

@@ -401,4 +401,184 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// pass_x with asynchronous staging: the CTA first copies its spectrum rows, strain rows and Lame
+// rows into shared memory with cp.async (16-byte granules, L2 only), so that all loads are in flight
+// at once, then runs the same transform / update / stress / transform sequence as pass_x_c_kernel
+// from shared memory.  Meant for small CTAs (few lines), several resident per SM.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <typename R, int N>
+__host__ __device__ constexpr int xa_spec_pitch() {  // complex elements per staged spectrum row (16-byte multiple)
+  return ((N / 2 + 1) * (int)sizeof(typename C<R>::T) + 15) / 16 * 16 / (int)sizeof(typename C<R>::T);
+}
+
+template <typename R, int N>
+__host__ __device__ constexpr size_t xa_smem_bytes(int lines) {
+  typedef typename C<R>::T T;
+  return sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16) + 6 * lines * xa_spec_pitch<R, N>()) +
+         sizeof(R) * (size_t)(8 * lines * N);
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(512) pass_x_a_kernel(typename C<R>::T* __restrict__ spec, R* __restrict__ eps,
+                                                       const R* __restrict__ lam, const R* __restrict__ mu,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d, int lines,
+                                                       int flags, const float* __restrict__ corr,
+                                                       const double* __restrict__ corr_mean,
+                                                       const SolveState* __restrict__ st) {
+  typedef typename C<R>::T T;
+  typedef CPlan<N> P;
+  if (st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LP = N + N / 16;
+  constexpr int NH = N / 2 + 1;
+  constexpr int SP = xa_spec_pitch<R, N>();
+  T* sspec = reinterpret_cast<T*>(smem_raw);                 // [6][lines][SP]
+  T* twl = sspec + 6 * lines * SP;                           // [N]
+  T* buf = twl + N;                                          // [3 lines][LP]
+  R* sst = reinterpret_cast<R*>(buf + 3 * lines * LP);       // [8][lines][N]: eps 0..5, lambda, mu
+  const long long nlines = (long long)d.n2 * d.n3;
+  const long long line0 = (long long)blockIdx.x * lines;
+  const bool have_delta = (flags & PX_DELTA) != 0;
+  const bool zero = (flags & PX_ZERO) != 0;
+  // ---- stage everything this CTA reads
+  {
+    constexpr int spec_chunks = SP * (int)sizeof(T) / 16;     // 16-byte granules per spectrum row
+    constexpr int row_chunks = N * (int)sizeof(R) / 16;      // per real row
+    const int nsp = have_delta ? 6 * lines * spec_chunks : 0;
+    const int nre = (zero ? 2 : 8) * lines * row_chunks;
+    for (int i = threadIdx.x; i < nsp + nre; i += blockDim.x) {
+      if (i < nsp) {
+        const int ch = i % spec_chunks, cl = i / spec_chunks;
+        const int l = cl % lines, c = cl / lines;
+        const long long li = line0 + l;
+        if (li >= nlines) continue;
+        cp_async16(reinterpret_cast<unsigned char*>(sspec + (c * lines + l) * SP) + 16 * ch,
+                   reinterpret_cast<const unsigned char*>(spec + c * d.S + li * d.P) + 16 * ch);
+      } else {
+        const int j = i - nsp;
+        const int ch = j % row_chunks, ql = j / row_chunks;
+        const int l = ql % lines, q0 = ql / lines;
+        const int q = zero ? 6 + q0 : q0;
+        const long long li = line0 + l;
+        if (li >= nlines) continue;
+        const R* src = q < 6 ? eps + q * d.N + li * N : (q == 6 ? lam + li * N : mu + li * N);
+        cp_async16(reinterpret_cast<unsigned char*>(sst + (q * lines + l) * N) + 16 * ch,
+                   reinterpret_cast<const unsigned char*>(src) + 16 * ch);
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
+  cp_async_wait_all();
+  __syncthreads();
+  const int t = threadIdx.x % P::T, fl = threadIdx.x / P::T;   // fl = pair * lines + l
+  const int p = fl / lines, l = fl % lines;
+  const SLine<T, true> sl{buf + fl * LP, 1};
+  T v[P::E];
+  if (have_delta) {
+    const T* A = sspec + (2 * p * lines + l) * SP;
+    const T* B = sspec + ((2 * p + 1) * lines + l) * SP;
+#pragma unroll
+    for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+      for (int r = 0; r < P::R(0); ++r) {
+        const int x = cin_idx<N, 0>(t, b, r);
+        const int k = x < NH ? x : N - x;
+        T a = A[k], bb = B[k];
+        if (k == 0 || 2 * k == N) { a.y = 0; bb.y = 0; }
+        T z;
+        if (x < NH) { z.x = a.x - bb.y; z.y = a.y + bb.x; }      // A + iB
+        else { z.x = a.x + bb.y; z.y = -a.y + bb.x; }            // conj(A) + i conj(B)
+        v[b * P::R(0) + r] = z;
+      }
+    cfft<N, true>(v, sl, t, twl);
+    constexpr int RL = P::R(P::NST - 1);
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  }
+  __syncthreads();
+  double cm[6];
+  if (corr) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cm[c] = corr_mean[c];
+  }
+  for (int i = threadIdx.x; i < lines * N; i += blockDim.x) {
+    const int x = i % N, ll = i / N;
+    const long long lj = line0 + ll;
+    if (lj >= nlines) continue;
+    const long long vv = lj * N + x;
+    const int px = x + (x >> 4);
+    R e[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = zero ? (R)0 : sst[(c * lines + ll) * N + x];
+    if (have_delta) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const T z = buf[(q * lines + ll) * LP + px];
+        e[2 * q] += z.x;
+        e[2 * q + 1] += z.y;
+      }
+    }
+    if (corr) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] += (R)((double)corr[c * d.N + vv] - cm[c]);
+    }
+    if (have_delta || zero || corr) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) eps[c * d.N + vv] = e[c];
+    }
+    const R la = sst[(6 * lines + ll) * N + x], m2 = (R)2 * sst[(7 * lines + ll) * N + x];
+    const R ltr = la * (e[0] + e[1] + e[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T z;
+      z.x = m2 * e[2 * q] + (q < 2 ? ltr : (R)0);        // 11, 33, 13
+      z.y = m2 * e[2 * q + 1] + (q == 0 ? ltr : (R)0);   // 22, 23, 12
+      buf[(q * lines + ll) * LP + px] = z;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) v[b * P::R(0) + r] = sl[cin_idx<N, 0>(t, b, r)];
+  __syncthreads();
+  cfft<N, false>(v, sl, t, twl);
+  {
+    constexpr int RL = P::R(P::NST - 1);
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * lines * NH; i += blockDim.x) {
+    const int k = i % NH, f = i / NH;
+    const int q = f / lines, ll = f % lines;
+    const long long lj = line0 + ll;
+    if (lj >= nlines) continue;
+    const T* line = buf + f * LP;
+    const int kn = (N - k) % N;
+    const T zk = line[k + (k >> 4)];
+    const T zn = line[kn + (kn >> 4)];
+    T A, B;
+    A.x = (R)0.5 * (zk.x + zn.x); A.y = (R)0.5 * (zk.y - zn.y);
+    B.x = (R)0.5 * (zk.y + zn.y); B.y = (R)-0.5 * (zk.x - zn.x);
+    const long long row = lj * d.P;
+    spec[(2 * q) * d.S + row + k] = A;
+    spec[(2 * q + 1) * d.S + row + k] = B;
+  }
+}
+
 }  // namespace gfp

@@ -379,6 +379,7 @@ struct LaunchCfg {
   int cx_lines;             // lines per CTA of the register-FFT x-pass (0: default)
   const void* ztmap;        // host CUtensorMap of the spectrum for TMA z-tiles of z_cols columns, or null
   int z_tma;                // use the TMA-fed z-pass when eligible (1) or the register-FFT one (0)
+  int x_async;              // register-FFT x-pass with cp.async staging (1) or direct loads (0)
 };
 
 template <typename R>

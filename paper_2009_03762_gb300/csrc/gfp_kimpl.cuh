@@ -17,6 +17,7 @@ cudaError_t Passes<R>::setup() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_gamma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 #define GFP_SET(N)                                                                                          \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_x_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_x_a_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -59,10 +60,20 @@ template <typename R, int N> inline int cx_lines_max() {
 }
 
 template <typename R, int N>
-inline void launch_x_c(cudaStream_t s, int want_lines, typename C<R>::T* spec, R* eps, const R* lam, const R* mu,
-                       const typename C<R>::T* tw, const Dims& d, int flags, const float* corr, const double* corr_mean,
-                       const SolveState* st) {
+inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>::T* spec, R* eps, const R* lam,
+                       const R* mu, const typename C<R>::T* tw, const Dims& d, int flags, const float* corr,
+                       const double* corr_mean, const SolveState* st) {
   typedef typename C<R>::T T;
+  if (async) {
+    int lines = want_lines > 0 ? want_lines : 2;
+    lines = std::min(lines, 512 / (3 * CPlan<N>::T));
+    while (lines > 1 && xa_smem_bytes<R, N>(lines) > 200 * 1024) --lines;
+    const long long nlines = (long long)d.n2 * d.n3;
+    const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
+    pass_x_a_kernel<R, N><<<blocks, 3 * lines * CPlan<N>::T, xa_smem_bytes<R, N>(lines), s>>>(
+        spec, eps, lam, mu, tw, d, lines, flags, corr, corr_mean, st);
+    return;
+  }
   const int lines = want_lines > 0 ? std::min(want_lines, cx_lines_max<R, N>()) : cx_lines_max<R, N>();
   const long long nlines = (long long)d.n2 * d.n3;
   const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
@@ -77,7 +88,7 @@ void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, con
                        const SolveState* st) {
   switch (d.n1) {
 #define GFP_CASE(N) \
-    case N: launch_x_c<R, N>(s, lc.cx_lines, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, st); return;
+    case N: launch_x_c<R, N>(s, lc.cx_lines, lc.x_async, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, st); return;
     GFP_FOR_CSIZES(GFP_CASE)
 #undef GFP_CASE
     default: break;
