@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + N;                          // [k3][6][cols]
   __shared__ double red[32];
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + N;                          // [3 lines][N + N/16] (padded line-major)
   constexpr int LP = N + N / 16;

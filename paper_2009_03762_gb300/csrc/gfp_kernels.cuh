@@ -122,7 +122,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
                               const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
   if (st->done) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* bufa = twl + d.n1;                      // [3 pairs][lines][n1], two ping-pong copies
   T* bufb = bufa + 3 * lines * d.n1;
@@ -236,7 +236,7 @@ __global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typenam
                               FftPlan plan, Dims d, int cols, const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
   if (st->done) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + d.n2;                       // [n2][cols], plus a ping-pong copy
   T* buf2 = buf + d.n2 * cols;
@@ -275,7 +275,7 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
                                     SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
   typedef typename C<R>::T T;
   if (st->done) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + d.n3;                       // [n3][6][cols], plus a ping-pong copy
   T* buf2 = buf + d.n3 * 6 * cols;

@@ -131,7 +131,7 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
 #define GFP_CASE(N)                                                                                           \
     case N: {                                                                                                 \
       const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
-      const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols);                                       \
+      const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols) + 128;                                 \
       if (lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 && smt <= 220 * 1024) {                    \
         const int ntiles = ntx * d.n2;                                                                        \
         const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \

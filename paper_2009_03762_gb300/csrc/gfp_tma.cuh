@@ -70,15 +70,22 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // TMA destinations must be 128-byte aligned: align the dynamic region by hand (the launch adds
+  // 128 bytes for this)
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int tile_elems = 6 * N * cols;
   T* tiles[2];
-  tiles[0] = reinterpret_cast<T*>(smem_raw);
+  tiles[0] = reinterpret_cast<T*>(base);
   tiles[1] = tiles[0] + tile_elems;
   T* twl = tiles[1] + tile_elems;
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ double red[32];
   __shared__ int abort_flag;
+  if ((smem_u32(tiles[0]) & 127u) != 0 || (smem_u32(tiles[1]) & 127u) != 0) {  // never issue a misaligned TMA
+    if (threadIdx.x == 0) atomicExch(&st->done, (int)DONE_TIMEOUT);
+    return;
+  }
   for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
