@@ -141,6 +141,131 @@ __global__ void corr_mean_final_kernel(const double* __restrict__ part, int nb, 
   }
 }
 
+
+// ---- discrete Green operator (Algorithm D-3D): alias-sum table, residual, mean stress
+// Gamma^c_ijab(omega) = -(1/(4 mu_H)) [d_ia S2_bj + d_ib S2_aj + d_ja S2_bi + d_jb S2_ai] + c/mu_H S4_ijab,
+// S2_ab = sum_nu w k_a k_b / |k|^2, S4_ijab = sum_nu w k_i k_j k_a k_b / |k|^4, w = prod_r s_r^power,
+// k = 2 pi (nu n + omega) / (n h), c = (lambda_H + mu_H) / (lambda_H + 2 mu_H); Gamma^c(0) = 0.
+__constant__ int c_mono4[3][3][3][3];  // index of the degree-4 monomial k_i k_j k_a k_b
+__constant__ int c_mono2[3][3];        // index of the degree-2 monomial k_a k_b
+
+__global__ void dgo_table_kernel(double* __restrict__ tab, Dims d, const double* __restrict__ w1,
+                                 const double* __restrict__ w2, const double* __restrict__ w3, int m1, int m2, int m3,
+                                 double h, double lam_h, double mu_h) {
+  const long long npts = (long long)d.n1h * d.n2 * d.n3;
+  const double two_pi = 6.283185307179586476925;
+  const double cc = (lam_h + mu_h) / (lam_h + 2.0 * mu_h);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < npts;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int o1 = (int)(idx % d.n1h);
+    const long long rest = idx / d.n1h;
+    const int o2 = (int)(rest % d.n2), o3 = (int)(rest / d.n2);
+    double S2[6] = {0, 0, 0, 0, 0, 0};
+    double S4[15];
+    for (int q = 0; q < 15; ++q) S4[q] = 0.0;
+    if (o1 != 0 || o2 != 0 || o3 != 0) {
+      for (int v3 = -m3; v3 < m3; ++v3) {
+        const double s3 = w3[o3 * 2 * m3 + (v3 + m3)];
+        if (s3 == 0.0) continue;
+        const double k3 = two_pi * (double)((long long)v3 * d.n3 + o3) / ((double)d.n3 * h);
+        for (int v2 = -m2; v2 < m2; ++v2) {
+          const double s2 = w2[o2 * 2 * m2 + (v2 + m2)];
+          if (s2 == 0.0) continue;
+          const double k2 = two_pi * (double)((long long)v2 * d.n2 + o2) / ((double)d.n2 * h);
+          const double s23 = s2 * s3;
+          for (int v1 = -m1; v1 < m1; ++v1) {
+            const double s1 = w1[o1 * 2 * m1 + (v1 + m1)];
+            if (s1 == 0.0) continue;
+            const double k1 = two_pi * (double)((long long)v1 * d.n1 + o1) / ((double)d.n1 * h);
+            const double kk = k1 * k1 + k2 * k2 + k3 * k3;
+            if (kk == 0.0) continue;
+            const double w = s1 * s23;
+            const double a = w / kk, b = a / kk;
+            const double k[3] = {k1, k2, k3};
+            S2[0] += a * k1 * k1; S2[1] += a * k2 * k2; S2[2] += a * k3 * k3;
+            S2[3] += a * k2 * k3; S2[4] += a * k1 * k3; S2[5] += a * k1 * k2;
+            int q = 0;
+            for (int i = 0; i < 3; ++i)
+              for (int j = i; j < 3; ++j)
+                for (int p = j; p < 3; ++p)
+                  for (int r = p; r < 3; ++r, ++q) S4[q] += b * k[i] * k[j] * k[p] * k[r];
+          }
+        }
+      }
+    }
+    // 6x6 Mandel matrix, upper triangle
+    const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
+    auto s2 = [&](int a, int b) { return S2[c_mono2[a][b]]; };
+    auto dl = [](int a, int b) { return a == b ? 1.0 : 0.0; };
+    const long long S = d.S;
+    const long long pos = ((long long)o3 * d.n2 + o2) * d.P + o1;
+    int q = 0;
+    for (int P = 0; P < 6; ++P)
+      for (int Q = P; Q < 6; ++Q, ++q) {
+        const int i = vi[P], j = vj[P], a = vi[Q], b = vj[Q];
+        double g = -(dl(i, a) * s2(b, j) + dl(i, b) * s2(a, j) + dl(j, a) * s2(b, i) + dl(j, b) * s2(a, i)) /
+                       (4.0 * mu_h) +
+                   cc / mu_h * S4[c_mono4[i][j][a][b]];
+        const double f = (P < 3 ? 1.0 : 1.41421356237309504880) * (Q < 3 ? 1.0 : 1.41421356237309504880);
+        tab[q * S + pos] = (o1 == 0 && o2 == 0 && o3 == 0) ? 0.0 : f * g;
+      }
+  }
+}
+
+// eta_D = sqrt(sum of partials) / (sqrt(N) ||E_bar||_F); one block, fixed order.
+__global__ void reduce_dgo_kernel(const double* __restrict__ partials, int np, double enorm, SolveState* st,
+                                  double* hist, int hist_cap) {
+  if (st->done) return;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double eta = enorm > 0.0 ? sqrt(sh[0]) / enorm : (sh[0] > 0.0 ? INFINITY : 0.0);
+    const int it = st->it + 1;
+    st->it = it;
+    const double prev = st->eta;
+    st->eta = eta;
+    if (hist && it - 1 < hist_cap) hist[it - 1] = eta;
+    if (!(eta == eta) || isinf(eta)) st->done = 3;
+    else if (eta < st->tol) st->done = 1;
+    else {
+      if (it > 1 && eta > prev) st->growth += 1; else st->growth = 0;
+      if (st->growth >= 50) st->done = 3;
+      else if (it >= st->maxit) st->done = 2;
+    }
+  }
+}
+
+// Mean stress sum(C : eps) per component, FP64, per-block partials (stage 1).
+__global__ void stress_sum_partial_kernel(const double* __restrict__ eps, const double* __restrict__ lam,
+                                          const double* __restrict__ mu, long long N, double* __restrict__ part) {
+  __shared__ double sh[6][256];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double e[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps[c * N + i];
+    const double ltr = lam[i] * (e[0] + e[1] + e[2]), m2 = 2.0 * mu[i];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += m2 * e[c] + (c < 3 ? ltr : 0.0);
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
 }  // namespace gfp
 
 // ------------------------------------------------------------------------------- the grid
@@ -188,6 +313,10 @@ struct gfp_grid_s {
   bool mixed_ready = false;
   bool lam32_valid = false;
   CUtensorMap zmap64, zmap32;  // TMA descriptors of the z-tiles for lc64 / lc32
+  // discrete Green operator table and the key it was built for
+  double* dgo = nullptr;
+  double dgo_key[4] = {0, 0, 0, 0};  // lambda_H, mu_H, m, valid
+  double* xpart = nullptr;           // per-CTA partials of the x-pass (DGO residual), n2 n3 entries
 };
 
 
@@ -364,6 +493,7 @@ void free_grid(gfp_grid g) {
   cudaFree(g->lam32); cudaFree(g->mu32); cudaFree(g->eps32); cudaFree(g->vsrc);
   for (int r = 0; r < 3; ++r) { cudaFree(g->tw32[r]); cudaFree(g->tabA32[r]); cudaFree(g->tabB32[r]); }
   cudaFree(g->st_in); cudaFree(g->cmean); cudaFree(g->cpart);
+  cudaFree(g->dgo); cudaFree(g->xpart);
   if (g->st_host) cudaFreeHost(g->st_host);
   if (g->st_in_host) cudaFreeHost(g->st_in_host);
   delete g;
@@ -458,6 +588,7 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   int status = GFP_OK;
   if (s.done == 2 || s.done == 0) status = GFP_ERR_NOT_CONVERGED;
   if (s.done == 3) status = GFP_ERR_DIVERGED;
+  if (s.done == DONE_TIMEOUT) status = GFP_ERR_DEVICE_TIMEOUT;
   if (out) {
     out->iters = s.it;
     out->outer = 0;
@@ -587,6 +718,7 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     const SolveState so = *g->st_host;
     if (so.done == 1) { status = GFP_OK; break; }
     if (so.done == 3) { status = GFP_ERR_DIVERGED; break; }
+    if (so.done == DONE_TIMEOUT) { status = GFP_ERR_DEVICE_TIMEOUT; break; }
     if (inner_total >= maxit) { status = GFP_ERR_NOT_CONVERGED; break; }
     // inner solve of the correction equation from a zero correction
     SolveState si = s0;
@@ -608,6 +740,7 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     }
     inner_total += g->st_in_host->it;
     if (g->st_in_host->done == 3) { status = GFP_ERR_DIVERGED; break; }
+    if (g->st_in_host->done == DONE_TIMEOUT) { status = GFP_ERR_DEVICE_TIMEOUT; break; }
     corr_mean_partial_kernel<<<cvb, 256, 0, g->stream>>>(g->eps32, d.N, g->cpart);
     corr_mean_final_kernel<<<1, 32, 0, g->stream>>>(g->cpart, cvb, d.N, g->cmean);
     // the next outer pass re-arms the FP64 state (it counts outer passes; never stops on maxit)
@@ -624,6 +757,161 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     for (int c = 0; c < 6; ++c) out->sigma_mean[c] = s.T0[c] / (double)d.N;
     out->status = status;
     if (out->residual_history && out->history_cap > 0) out->residual_history[0] = s.eta;
+  }
+  return status;
+}
+
+// Sinc weights s_j = sinc(pi j / n) of axis r raised to `power`, for omega in [0, n) (rows) and
+// nu in [-m, m) (columns); exact zeros where j = 0 mod n, j != 0.
+void dgo_weights(int n, int m, int power, std::vector<double>& w) {
+  const double pi = 3.14159265358979323846;
+  w.assign((size_t)n * 2 * m, 0.0);
+  for (int o = 0; o < n; ++o)
+    for (int v = -m; v < m; ++v) {
+      const long long j = (long long)v * n + o;
+      double s;
+      if (j == 0) s = 1.0;
+      else if (j % n == 0) s = 0.0;
+      else { const double x = pi * (double)j / (double)n; s = std::sin(x) / x; }
+      w[(size_t)o * 2 * m + (v + m)] = power == 2 ? s * s : s;
+    }
+}
+
+std::once_flag g_mono_once;
+
+int ensure_dgo(gfp_grid g, int dgo_m) {
+  const Dims& d = g->d;
+  const int ns[3] = {g->n1, g->n2, g->n3};
+  int ms[3];
+  for (int r = 0; r < 3; ++r) ms[r] = std::max(1, dgo_m > 0 ? dgo_m : ns[r] / 2);
+  if (g->dgo && g->dgo_key[3] == 1.0 && g->dgo_key[0] == g->lam_h && g->dgo_key[1] == g->mu_h &&
+      g->dgo_key[2] == (double)dgo_m)
+    return GFP_OK;
+  static int mono_err = 0;
+  std::call_once(g_mono_once, [] {
+    int m4[3][3][3][3], m2[3][3];
+    int q = 0, idx4[3][3][3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = i; j < 3; ++j)
+        for (int p = j; p < 3; ++p)
+          for (int r = p; r < 3; ++r) idx4[i][j][p][r] = q++;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int p = 0; p < 3; ++p)
+          for (int r = 0; r < 3; ++r) {
+            int v[4] = {i, j, p, r};
+            std::sort(v, v + 4);
+            m4[i][j][p][r] = idx4[v[0]][v[1]][v[2]][v[3]];
+          }
+    const int s2map[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) m2[a][b] = s2map[a][b];
+    if (cudaMemcpyToSymbol(c_mono4, m4, sizeof(m4)) != cudaSuccess) mono_err = 1;
+    if (cudaMemcpyToSymbol(c_mono2, m2, sizeof(m2)) != cudaSuccess) mono_err = 1;
+  });
+  if (mono_err) return GFP_ERR_CUDA;
+  if (!g->dgo) GFP_CU(cudaMalloc(&g->dgo, sizeof(double) * 21 * (size_t)d.S));
+  double* w[3] = {nullptr, nullptr, nullptr};
+  for (int r = 0; r < 3; ++r) {
+    std::vector<double> hw;
+    dgo_weights(ns[r], ms[r], 2, hw);
+    GFP_CU(cudaMalloc(&w[r], sizeof(double) * hw.size()));
+    GFP_CU(cudaMemcpy(w[r], hw.data(), sizeof(double) * hw.size(), cudaMemcpyHostToDevice));
+  }
+  GFP_CU(cudaMemsetAsync(g->dgo, 0, sizeof(double) * 21 * (size_t)d.S, g->stream));
+  const long long npts = (long long)d.n1h * d.n2 * d.n3;
+  dgo_table_kernel<<<(int)std::min<long long>(4096, (npts + 127) / 128), 128, 0, g->stream>>>(
+      g->dgo, d, w[0], w[1], w[2], ms[0], ms[1], ms[2], g->h, g->lam_h, g->mu_h);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  for (int r = 0; r < 3; ++r) cudaFree(w[r]);
+  if (e != cudaSuccess) { note_error(e, __LINE__); return cuda_status(e); }
+  g->dgo_key[0] = g->lam_h;
+  g->dgo_key[1] = g->mu_h;
+  g->dgo_key[2] = (double)dgo_m;
+  g->dgo_key[3] = 1.0;
+  return GFP_OK;
+}
+
+// Algorithm D-3D in the polarization form with s^2 weights: eps = E_bar + F+ Gamma^c F- [(C - C_H) eps];
+// iteration `it` forms eps^(it) in the x-pass of the next launch and the residual
+// ||eps^(it) - eps^(it-1)|| / (sqrt(N) ||E_bar||_F) is reduced right after it.
+int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, int maxit, gfp_result* out) {
+  int rc = ensure_dgo(g, sc->dgo_m);
+  if (rc) return rc;
+  rc = ensure_tables(g, OP_AFB_R);  // the DGO path does not read k-tables; keep them valid
+  if (rc) return rc;
+  rc = ensure_hist(g, std::max(maxit, 1));
+  if (rc) return rc;
+  const Dims& d = g->d;
+  if (!g->xpart) GFP_CU(cudaMalloc(&g->xpart, sizeof(double) * (size_t)d.n2 * d.n3));
+  GFP_CU(cudaMemsetAsync(g->xpart, 0, sizeof(double) * (size_t)d.n2 * d.n3, g->stream));
+  GammaParams<double> gp = gamma_params<double>(g, OP_AFB_R, g->tabA, g->tabB);
+  gp.dgo = g->dgo;
+  PolarParams pp;
+  for (int c = 0; c < 6; ++c) pp.E[c] = E[c];
+  pp.lam_h = g->lam_h;
+  pp.mu_h = g->mu_h;
+  pp.partials = g->xpart;
+  const double en2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + 2.0 * (E[3] * E[3] + E[4] * E[4] + E[5] * E[5]);
+  const double enorm = std::sqrt(en2) * std::sqrt((double)d.N);
+  fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, d.N, E[0], E[1],
+                                                                                          E[2], E[3], E[4], E[5]);
+  SolveState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.maxit = maxit;
+  s0.tol = tol;
+  s0.eta = INFINITY;
+  s0.eta_min = INFINITY;
+  *g->st_host = s0;
+  GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+  const int np = d.n2 * d.n3;
+  int launched = 0, chunk = 2;
+  while (launched < maxit + 1) {
+    const int nb = std::min(chunk, maxit + 1 - launched);
+    for (int b = 0; b < nb; ++b) {
+      const int j = launched + b;
+      Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+                             PX_POLAR | (j > 0 ? PX_DELTA : 0), nullptr, nullptr, g->st, &pp);
+      if (j > 0) reduce_dgo_kernel<<<1, 256, 0, g->stream>>>(g->xpart, np, enorm, g->st, g->hist, g->hist_cap);
+      Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+      Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_DGO,
+                             nullptr);
+      Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    }
+    launched += nb;
+    GFP_CU(cudaGetLastError());
+    GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
+    GFP_CU(cudaStreamSynchronize(g->stream));
+    if (g->st_host->done) break;
+    chunk = std::min(chunk * 2, 64);
+  }
+  const SolveState s = *g->st_host;
+  // mean stress of the final strain
+  const int sb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+  stress_sum_partial_kernel<<<sb, 256, 0, g->stream>>>(g->eps, g->lam, g->mu, d.N, g->scratch);
+  std::vector<double> part(6 * (size_t)sb);
+  GFP_CU(cudaMemcpyAsync(part.data(), g->scratch, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, g->stream));
+  GFP_CU(cudaStreamSynchronize(g->stream));
+  g->state_iters = s.it;
+  int status = GFP_OK;
+  if (s.done == 2 || s.done == 0) status = GFP_ERR_NOT_CONVERGED;
+  if (s.done == 3) status = GFP_ERR_DIVERGED;
+  if (s.done == DONE_TIMEOUT) status = GFP_ERR_DEVICE_TIMEOUT;
+  if (out) {
+    out->iters = s.it;
+    out->outer = 0;
+    out->residual = s.eta;
+    for (int c = 0; c < 6; ++c) {
+      double acc = 0.0;
+      for (int b = 0; b < sb; ++b) acc += part[(size_t)b * 6 + c];
+      out->sigma_mean[c] = acc / (double)d.N;
+    }
+    out->status = status;
+    if (out->residual_history && out->history_cap > 0) {
+      const int nh = std::min(out->history_cap, std::min(s.it, g->hist_cap));
+      if (nh > 0) GFP_CU(cudaMemcpy(out->residual_history, g->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    }
   }
   return status;
 }
@@ -766,7 +1054,7 @@ int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_gri
   g->np_max = d.n1h * d.n2;  // enough for any z-tile width (one column per CTA)
   A((void**)&g->partials, sizeof(double) * g->np_max);
   A((void**)&g->st, sizeof(SolveState));
-  A((void**)&g->scratch, sizeof(double) * 4 * 1024);
+  A((void**)&g->scratch, sizeof(double) * 8 * 1024);
   A((void**)&g->bad, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&g->st_host, sizeof(SolveState));
   if (e != cudaSuccess) { note_error(e, __LINE__); free_grid(g); return cuda_status(e); }
@@ -839,7 +1127,10 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
     g->resume_pending = false;
     return solve_mixed(g, sc, E, tol, maxit, out);
   }
-  if (sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
+  if (sc->op == OP_DGO) {
+    g->resume_pending = false;
+    return solve_dgo(g, sc, E, tol, maxit, out);
+  }
   const bool resume = g->resume_pending;
   g->resume_pending = false;
   return solve_fp64(g, sc, E, tol, maxit, out, resume);

@@ -230,6 +230,12 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
       continue;
     }
     T o[6];
+    if (mode == PZ_DGO) {
+      dgo_apply_point<R>(tt, gp.dgo, vi, d.S, gp.invN, o);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+      continue;
+    }
     gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
     if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
       T o2[6];
@@ -274,12 +280,13 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
                                                        const R* __restrict__ lam, const R* __restrict__ mu,
                                                        const typename C<R>::T* __restrict__ tw, Dims d, int lines,
                                                        int flags, const float* __restrict__ corr,
-                                                       const double* __restrict__ corr_mean,
+                                                       const double* __restrict__ corr_mean, PolarParams pp,
                                                        const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + N;                          // [3 lines][N + N/16] (padded line-major)
   constexpr int LP = N + N / 16;
@@ -322,6 +329,8 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
       for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
   }
   __syncthreads();
+  const bool polar = (flags & PX_POLAR) != 0;
+  double dacc = 0.0;
   double cm[6];
   if (corr) {
 #pragma unroll
@@ -342,11 +351,17 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
       for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + vv];
     }
     if (have_delta) {
+      R dd[6];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const T z = buf[(q * lines + ll) * LP + px];
-        e[2 * q] += z.x;
-        e[2 * q + 1] += z.y;
+        dd[2 * q] = z.x;
+        dd[2 * q + 1] = z.y;
+      }
+      if (polar) dacc += polar_update<R>(e, dd, pp);
+      else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] += dd[c];
       }
     }
     if (corr) {
@@ -357,15 +372,15 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
 #pragma unroll
       for (int c = 0; c < 6; ++c) eps[c * d.N + vv] = e[c];
     }
-    const R la = lam[vv], m2 = (R)2 * mu[vv];
-    const R ltr = la * (e[0] + e[1] + e[2]);
+    T zz[3];
+    if (polar) pack_stress<R>(e, lam[vv] - (R)pp.lam_h, mu[vv] - (R)pp.mu_h, zz);
+    else pack_stress<R>(e, lam[vv], mu[vv], zz);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      T z;
-      z.x = m2 * e[2 * q] + (q < 2 ? ltr : (R)0);        // 11, 33, 13
-      z.y = m2 * e[2 * q + 1] + (q == 0 ? ltr : (R)0);   // 22, 23, 12
-      buf[(q * lines + ll) * LP + px] = z;
-    }
+    for (int q = 0; q < 3; ++q) buf[(q * lines + ll) * LP + px] = zz[q];
+  }
+  if (polar && have_delta) {
+    const double sum = block_sum(dacc, red);
+    if (threadIdx.x == 0) pp.partials[blockIdx.x] = sum;
   }
   __syncthreads();
 #pragma unroll

@@ -25,6 +25,10 @@ struct Dims {
   long long S;  // spectrum component stride = n3 n2 P
 };
 
+// SolveState::done values besides 0 (running): 1 converged, 2 maxit, 3 diverged, DONE_TIMEOUT when a
+// bounded device-side wait gave up.
+enum { DONE_TIMEOUT = 4 };
+
 // Device-side solver state; one per solve, reset by the host before the first iteration.
 struct SolveState {
   int it;          // iterations done
@@ -48,7 +52,42 @@ struct GammaParams {
   R c_lm;              // (lambda_H + mu_H) / (mu_H (lambda_H + 2 mu_H))
   R invN;
   int nyq_avg;         // average Gamma over the Hermitian partner on Nyquist planes (F, HC)
+  const double* dgo;   // DGO: 21 Mandel entries per half-spectrum point, [21][k3][k2][P] (mode PZ_DGO)
 };
+
+// Discrete Green operator (Algorithm D) at one half-spectrum point: out = invN * Gamma^c t, with
+// Gamma^c stored as the upper triangle of its symmetric 6x6 Mandel matrix (basis 11,22,33,23,13,12
+// with sqrt(2) on the shear components), 21 planes of stride S.
+template <typename R, typename T>
+__device__ __forceinline__ void dgo_apply_point(const T t[6], const double* __restrict__ tab, long long vi,
+                                                long long S, R invN, T out[6]) {
+  const R r2 = (R)1.41421356237309504880, ir2 = (R)0.70710678118654752440;
+  T a[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const R f = c < 3 ? (R)1 : r2;
+    a[c].x = f * t[c].x;
+    a[c].y = f * t[c].y;
+  }
+  T o[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) { o[c].x = 0; o[c].y = 0; }
+  int q = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j, ++q) {
+      const R m = (R)tab[q * S + vi];
+      o[i].x += m * a[j].x; o[i].y += m * a[j].y;
+      if (j != i) { o[j].x += m * a[i].x; o[j].y += m * a[i].y; }
+    }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const R f = (c < 3 ? (R)1 : ir2) * invN;
+    out[c].x = f * o[c].x;
+    out[c].y = f * o[c].y;
+  }
+}
 
 // v = t kt for a symmetric complex tensor t (components 11,22,33,23,13,12) and a real vector kt
 template <typename R, typename T>
@@ -109,7 +148,55 @@ __device__ __forceinline__ R tk_norm2(const T t[6], R k1, R k2, R k3) {
 // --------------------------------------------------------------------------------------------
 // pass_x: one CTA handles `lines` consecutive x1-lines (fixed i3, consecutive i2).
 // --------------------------------------------------------------------------------------------
-enum { PX_DELTA = 1, PX_ZERO = 2 };
+enum { PX_DELTA = 1, PX_ZERO = 2, PX_POLAR = 4 };
+
+// Polarization form of the discrete-Green-operator iteration (Algorithm D with the polarization of
+// Eloh2019): with PX_POLAR the x-pass forms eps = E_bar + inverse transform (instead of adding it),
+// accumulates ||eps_new - eps_old||_F^2 per CTA into partials[blockIdx.x] when PX_DELTA is set, and
+// transforms tau = (C - C_H) : eps instead of sigma = C : eps.
+struct PolarParams {
+  double E[6];
+  double lam_h, mu_h;
+  double* partials;
+};
+
+// Stress (or polarization) of one voxel, packed as the three complex pairs (11,22), (33,23), (13,12).
+template <typename R, typename T>
+__device__ __forceinline__ void pack_stress(const R e[6], R la, R mu, T z[3]) {
+  const R m2 = (R)2 * mu, ltr = la * (e[0] + e[1] + e[2]);
+  z[0].x = m2 * e[0] + ltr; z[0].y = m2 * e[1] + ltr;
+  z[1].x = m2 * e[2] + ltr; z[1].y = m2 * e[3];
+  z[2].x = m2 * e[4];       z[2].y = m2 * e[5];
+}
+
+// Polarization update of one voxel: e <- E_bar + d (d: the inverse transform), returns the squared
+// Frobenius norm of the change (shear components count twice).
+template <typename R>
+__device__ __forceinline__ double polar_update(R e[6], const R d[6], const PolarParams& pp) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const R en = (R)pp.E[c] + d[c];
+    const double df = (double)en - (double)e[c];
+    s += (c < 3 ? 1.0 : 2.0) * df * df;
+    e[c] = en;
+  }
+  return s;
+}
+
+// Block sum of one double per thread (thread 0 receives the result); all threads must call.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  }
+  return s;
+}
 
 // flags: PX_DELTA adds the inverse x-transform of the spectrum (the previous increment) to the state;
 // PX_ZERO starts from a zero state (not read, written as zeros).  corr (FP32, may be null) is an
@@ -119,10 +206,11 @@ template <typename R>
 __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict__ eps, const R* __restrict__ lam,
                               const R* __restrict__ mu, const typename C<R>::T* __restrict__ tw, FftPlan plan, Dims d,
                               int lines, int flags, const float* __restrict__ corr, const double* __restrict__ corr_mean,
-                              const SolveState* __restrict__ st) {
+                              PolarParams pp, const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* bufa = twl + d.n1;                      // [3 pairs][lines][n1], two ping-pong copies
   T* bufb = bufa + 3 * lines * d.n1;
@@ -167,6 +255,8 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
 #pragma unroll
     for (int c = 0; c < 6; ++c) cm[c] = corr_mean[c];
   }
+  const bool polar = (flags & PX_POLAR) != 0;
+  double dacc = 0.0;
   // state update, sigma = C : eps, repack sigma pairs for the forward transform
   for (int i = threadIdx.x; i < lines * n1; i += blockDim.x) {
     const int x = i % n1, l = i / n1;
@@ -182,11 +272,17 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
       for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + v];
     }
     if (have_delta) {
+      R dd[6];
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         const T z = buf[(p * lines + l) * n1 + x];
-        e[2 * p] += z.x;
-        e[2 * p + 1] += z.y;
+        dd[2 * p] = z.x;
+        dd[2 * p + 1] = z.y;
+      }
+      if (polar) dacc += polar_update<R>(e, dd, pp);
+      else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] += dd[c];
       }
     }
     if (corr) {
@@ -197,15 +293,15 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
 #pragma unroll
       for (int c = 0; c < 6; ++c) eps[c * d.N + v] = e[c];
     }
-    const R la = lam[v], m2 = (R)2 * mu[v];
-    const R ltr = la * (e[0] + e[1] + e[2]);
+    T zz[3];
+    if (polar) pack_stress<R>(e, lam[v] - (R)pp.lam_h, mu[v] - (R)pp.mu_h, zz);
+    else pack_stress<R>(e, lam[v], mu[v], zz);
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      T z;
-      z.x = m2 * e[2 * p] + (p < 2 ? ltr : (R)0);        // 11, 33, 13
-      z.y = m2 * e[2 * p + 1] + (p == 0 ? ltr : (R)0);   // 22, 23, 12
-      buf[(p * lines + l) * n1 + x] = z;
-    }
+    for (int p = 0; p < 3; ++p) buf[(p * lines + l) * n1 + x] = zz[p];
+  }
+  if (polar && have_delta) {
+    const double sum = block_sum(dacc, red);
+    if (threadIdx.x == 0) pp.partials[blockIdx.x] = sum;
   }
   __syncthreads();
   buf = fft_lines<false>(buf, buf == bufa ? bufb : bufa, twl, plan, LineLayout{tot_lines, 1, n1, false});
@@ -263,7 +359,7 @@ __global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typenam
 // pass_z_gamma: tile = all n3 rows x `cols` k1 columns x 6 components at fixed k2.
 // smem layout [k3][comp][col] so that line (comp, col) has element stride 6 cols.
 // --------------------------------------------------------------------------------------------
-enum { PZ_GAMMA = 0, PZ_RESIDUAL = 1, PZ_INNER = 2 };
+enum { PZ_GAMMA = 0, PZ_RESIDUAL = 1, PZ_INNER = 2, PZ_DGO = 3 };
 
 // mode PZ_GAMMA: Delta E = -Gamma0(kt) T / N, residual, T(0), inverse z (the FP64 or FP32 iteration).
 // mode PZ_RESIDUAL: residual and T(0) only; stores v = T kt (FP32, [3][k3][k2][P]) as the source of
@@ -338,6 +434,12 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
       continue;
     }
     T o[6];
+    if (mode == PZ_DGO) {
+      dgo_apply_point<R>(t, gp.dgo, vi, d.S, gp.invN, o);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+      continue;
+    }
     gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
     if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
       T o2[6];
@@ -388,7 +490,7 @@ struct Passes {
   static cudaError_t setup();   // opt-in shared memory limits
   static void pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, const R* lam, const R* mu, const T* tw,
                      const FftPlan& plan, const Dims& d, int flags, const float* corr, const double* corr_mean,
-                     const SolveState* st);
+                     const SolveState* st, const PolarParams* pp = nullptr);
   static void pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spec, const T* tw, const FftPlan& plan,
                      const Dims& d, const SolveState* st);
   static void pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw, const FftPlan& plan, const Dims& d,

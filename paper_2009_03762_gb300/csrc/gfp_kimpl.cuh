@@ -62,9 +62,9 @@ template <typename R, int N> inline int cx_lines_max() {
 template <typename R, int N>
 inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>::T* spec, R* eps, const R* lam,
                        const R* mu, const typename C<R>::T* tw, const Dims& d, int flags, const float* corr,
-                       const double* corr_mean, const SolveState* st) {
+                       const double* corr_mean, const PolarParams& pp, const SolveState* st) {
   typedef typename C<R>::T T;
-  if (async) {
+  if (async && !(flags & PX_POLAR)) {
     int lines = want_lines > 0 ? want_lines : 2;
     lines = std::min(lines, 512 / (3 * CPlan<N>::T));
     while (lines > 1 && xa_smem_bytes<R, N>(lines) > 200 * 1024) --lines;
@@ -79,16 +79,19 @@ inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>:
   const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
   const size_t sm = sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16));
   pass_x_c_kernel<R, N><<<blocks, 3 * lines * CPlan<N>::T, sm, s>>>(spec, eps, lam, mu, tw, d, lines, flags, corr,
-                                                                     corr_mean, st);
+                                                                     corr_mean, pp, st);
 }
 
 template <typename R>
 void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, const R* lam, const R* mu, const T* tw,
                        const FftPlan& plan, const Dims& d, int flags, const float* corr, const double* corr_mean,
-                       const SolveState* st) {
+                       const SolveState* st, const PolarParams* ppp) {
+  PolarParams pp;
+  if (ppp) pp = *ppp;
+  else { for (int c = 0; c < 6; ++c) pp.E[c] = 0; pp.lam_h = pp.mu_h = 0; pp.partials = nullptr; }
   switch (d.n1) {
 #define GFP_CASE(N) \
-    case N: launch_x_c<R, N>(s, lc.cx_lines, lc.x_async, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, st); return;
+    case N: launch_x_c<R, N>(s, lc.cx_lines, lc.x_async, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, pp, st); return;
     GFP_FOR_CSIZES(GFP_CASE)
 #undef GFP_CASE
     default: break;
@@ -97,7 +100,7 @@ void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, con
   const unsigned blocks = (unsigned)((nlines + lc.x_lines - 1) / lc.x_lines);
   const size_t sm = sizeof(T) * (size_t)(d.n1 + 6 * lc.x_lines * d.n1);
   pass_x_kernel<R><<<blocks, lc.x_threads, sm, s>>>(spec, eps, lam, mu, tw, plan, d, lc.x_lines, flags, corr,
-                                                     corr_mean, st);
+                                                     corr_mean, pp, st);
 }
 
 template <typename R>
@@ -132,7 +135,8 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
     case N: {                                                                                                 \
       const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
       const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols) + 128;                                 \
-      if (lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 && smt <= 220 * 1024) {                    \
+      if (mode != PZ_DGO && lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 &&        \
+          smt <= 220 * 1024) {                    \
         const int ntiles = ntx * d.n2;                                                                        \
         const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \
         pass_z_tma_kernel<R, N><<<gsz, th, smt, s>>>(*reinterpret_cast<const CUtensorMap*>(lc.ztmap), spec, tw, \

@@ -12,8 +12,6 @@
 
 namespace gfp {
 
-enum { DONE_TIMEOUT = 4 };
-
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
