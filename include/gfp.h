@@ -118,6 +118,17 @@ int gfp_effective_stiffness(gfp_grid g, const gfp_scheme* scheme, double tol, in
 int gfp_grad(gfp_grid g, const gfp_scheme* scheme, int I, int J, double tol, int maxit, double* dC_dlambda,
              double* dC_dmu, int where);
 
+/* Batched homogenization (no counterpart in the paper): the six Voigt load cases of `count` cells of
+ * possibly different sizes, mixed precision only (FP32 inner iterations, FP64 residual, mean strain and
+ * refinement; schemes CD, ACD, AHC, AFB_R).  Every (cell, load) pair is a slot with its own device
+ * state; one CUDA graph holds a window of every slot (one FP64 residual pass and 32 FP32 iterations) as
+ * parallel branches, and the graph is replayed until all slots reach eta < tol or maxit iterations.
+ * Converged slots turn into no-ops on the device.  C_eff_out: count x 36 (row-major Voigt per cell);
+ * iters_out (may be NULL): count x 6 inner iterations per load.  The cells must have their phases set.
+ * Slot buffers (about 230 bytes per voxel per load) are allocated for the call and freed at its end. */
+int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* scheme, double tol, int maxit, double* C_eff_out,
+                    int* iters_out);
+
 /* Checkpoint/resume: the strain field and the iteration count fully determine a solve's state. */
 int gfp_get_state(gfp_grid g, double* eps_dst, int* iters);
 int gfp_set_state(gfp_grid g, const double* eps_src, int iters);

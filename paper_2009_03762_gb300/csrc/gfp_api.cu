@@ -266,6 +266,46 @@ __global__ void stress_sum_partial_kernel(const double* __restrict__ eps, const 
   if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+
+// ---- batched solves: per-slot bookkeeping between the FP64 outer pass and the FP32 inner window
+struct BatchAcc {
+  int inner;  // inner iterations accumulated over the windows
+  int outer;  // FP64 outer passes
+};
+
+// Start the inner window of one (microstructure, load) slot after its FP64 residual pass: count the
+// previous window's iterations, then re-arm the inner state with the target max(tol/2, ratio eta_64)
+// and the reference stress norm of the outer pass; a converged slot leaves its inner state done.
+__global__ void batch_arm_kernel(const SolveState* __restrict__ st, SolveState* __restrict__ st_in, BatchAcc* acc,
+                                 double tol, double ratio, int window) {
+  if (threadIdx.x != 0) return;
+  acc->inner += st_in->it;
+  st_in->it = 0;
+  if (st->done) {
+    st_in->done = 1;
+    return;
+  }
+  acc->outer = st->it;
+  st_in->done = 0;
+  st_in->growth = 0;
+  st_in->maxit = window;
+  st_in->eta = INFINITY;
+  st_in->eta_min = INFINITY;
+  st_in->tol = fmax(0.5 * tol, ratio * st->eta);
+  for (int c = 0; c < 6; ++c) st_in->T0[c] = st->T0[c];
+}
+
+// 1 if every slot's outer state is done (converged, diverged or timed out).
+__global__ void batch_all_done_kernel(SolveState* const* __restrict__ sts, int n, int* flag) {
+  __shared__ int any_running;
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (sts[i]->done == 0) any_running = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any_running ? 0 : 1;
+}
+
 }  // namespace gfp
 
 // ------------------------------------------------------------------------------- the grid
@@ -1583,6 +1623,228 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   finalize_cfg(d, lc);
   refresh_ztmap(g, mixed);
   return GFP_OK;
+}
+
+}  // extern "C"
+
+// ---- batched homogenization: every (microstructure, Voigt load) pair is a slot with its own state;
+// one CUDA graph holds a window (FP64 residual pass + `window` FP32 inner iterations) for all slots as
+// parallel branches and is replayed until every slot has converged.
+namespace {
+
+struct BatchSlot {
+  gfp_grid g;
+  int load;
+  double* eps = nullptr;
+  float* eps32 = nullptr;
+  double2* spec = nullptr;
+  float2* vsrc = nullptr;
+  double* partials = nullptr;
+  SolveState* st = nullptr;
+  SolveState* st_in = nullptr;
+  double* cmean = nullptr;
+  double* cpart = nullptr;
+  BatchAcc* acc = nullptr;
+  cudaStream_t stream = nullptr;
+  LaunchCfg lc64, lc32;
+  CUtensorMap zm64, zm32;
+};
+
+void free_slot(BatchSlot& s) {
+  cudaFree(s.eps); cudaFree(s.eps32); cudaFree(s.spec); cudaFree(s.vsrc); cudaFree(s.partials);
+  cudaFree(s.st); cudaFree(s.st_in); cudaFree(s.cmean); cudaFree(s.cpart); cudaFree(s.acc);
+  if (s.stream) cudaStreamDestroy(s.stream);
+}
+
+void slot_window(BatchSlot& s, const GammaParams<double>& gp64, const GammaParams<float>& gp32, double tol,
+                 int window) {
+  gfp_grid g = s.g;
+  const Dims& d = g->d;
+  cudaStream_t st = s.stream;
+  const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+  Passes<double>::pass_x(st, s.lc64, s.spec, s.eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0, s.eps32, s.cmean,
+                         s.st);
+  Passes<double>::pass_y(st, s.lc64, false, s.spec, g->tw64[1], g->plan[1], d, s.st);
+  Passes<double>::pass_z(st, s.lc64, s.spec, g->tw64[2], g->plan[2], d, gp64, s.partials, s.st, PZ_RESIDUAL, s.vsrc);
+  launch_reduce_eta(st, s.partials, s.lc64.z_blocks, s.st, nullptr, 0);
+  batch_arm_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, s.acc, tol, kInnerReduction, window);
+  float2* spec32 = reinterpret_cast<float2*>(s.spec);
+  for (int k = 0; k < window; ++k) {
+    Passes<float>::pass_x(st, s.lc32, spec32, s.eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d,
+                          k == 0 ? PX_ZERO : PX_DELTA, nullptr, nullptr, s.st_in);
+    Passes<float>::pass_y(st, s.lc32, false, spec32, g->tw32[1], g->plan[1], d, s.st_in);
+    Passes<float>::pass_z(st, s.lc32, spec32, g->tw32[2], g->plan[2], d, gp32, s.partials, s.st_in, PZ_INNER, s.vsrc);
+    launch_reduce_eta(st, s.partials, s.lc32.z_blocks, s.st_in, nullptr, 0);
+    Passes<float>::pass_y(st, s.lc32, true, spec32, g->tw32[1], g->plan[1], d, s.st_in);
+  }
+  corr_mean_partial_kernel<<<cvb, 256, 0, st>>>(s.eps32, d.N, s.cpart);
+  corr_mean_final_kernel<<<1, 32, 0, st>>>(s.cpart, cvb, d.N, s.cmean);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol, int maxit, double* C_eff_out,
+                    int* iters_out) {
+  if (count < 1 || !grids || !scheme_ok(sc) || !(tol > 0.0) || maxit < 1 || !C_eff_out) return GFP_ERR_ARG;
+  if (sc->prec != GFP_MIXED || sc->op == OP_F || sc->op == OP_HC || sc->op == OP_DGO || sc->stop_rule != 0)
+    return GFP_ERR_UNSUPPORTED;
+  for (int i = 0; i < count; ++i)
+    if (!grids[i] || !grids[i]->phases) return GFP_ERR_ARG;
+  // shared per-grid data: FP32 Lame fields, tables, twiddles
+  for (int i = 0; i < count; ++i) {
+    gfp_grid g = grids[i];
+    int rc = ensure_mixed(g);
+    if (rc) return rc;
+    rc = ensure_tables(g, sc->op);
+    if (rc) return rc;
+    const int cvb = (int)std::min<long long>(1024, (g->d.N + 255) / 256);
+    if (!g->lam32_valid) {
+      to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->lam, g->lam32, g->d.N);
+      to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->mu, g->mu32, g->d.N);
+      g->lam32_valid = true;
+    }
+    GFP_CU(cudaStreamSynchronize(g->stream));
+  }
+  const int window = 32;
+  const int nslots = count * 6;
+  std::vector<BatchSlot> slots(nslots);
+  std::vector<SolveState*> st_ptrs(nslots);
+  int rc = GFP_OK;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  for (int i = 0; i < count; ++i)
+    for (int J = 0; J < 6; ++J) {
+      BatchSlot& s = slots[i * 6 + J];
+      gfp_grid g = grids[i];
+      const Dims& d = g->d;
+      s.g = g;
+      s.load = J;
+      A((void**)&s.eps, sizeof(double) * 6 * d.N);
+      A((void**)&s.eps32, sizeof(float) * 6 * d.N);
+      A((void**)&s.spec, sizeof(double2) * 6 * d.S);
+      A((void**)&s.vsrc, sizeof(float2) * 3 * d.S);
+      A((void**)&s.partials, sizeof(double) * (size_t)d.n1h * d.n2);
+      A((void**)&s.st, sizeof(SolveState));
+      A((void**)&s.st_in, sizeof(SolveState));
+      A((void**)&s.cmean, sizeof(double) * 6);
+      A((void**)&s.cpart, sizeof(double) * 6 * 1024);
+      A((void**)&s.acc, sizeof(BatchAcc));
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) break;
+      s.lc64 = g->lc64;
+      s.lc32 = g->lc32;
+      s.lc64.ztmap = encode_ztmap(&s.zm64, s.spec, d, s.lc64.z_cols, 8) ? &s.zm64 : nullptr;
+      s.lc32.ztmap = encode_ztmap(&s.zm32, s.spec, d, s.lc32.z_cols, 4) ? &s.zm32 : nullptr;
+      st_ptrs[i * 6 + J] = s.st;
+    }
+  int* d_flag = nullptr;
+  SolveState** d_sts = nullptr;
+  cudaStream_t main = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&d_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_sts, sizeof(SolveState*) * nslots);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_sts, st_ptrs.data(), sizeof(SolveState*) * nslots, cudaMemcpyHostToDevice);
+  // initial state of every slot: eps = E_J, zero correction, fresh outer and inner states
+  if (e == cudaSuccess) {
+    for (auto& s : slots) {
+      const Dims& d = s.g->d;
+      double E[6] = {0, 0, 0, 0, 0, 0};
+      E[s.load] = s.load < 3 ? 1.0 : 0.5;
+      fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, s.stream>>>(
+          s.eps, d.N, E[0], E[1], E[2], E[3], E[4], E[5]);
+      cudaMemsetAsync(s.eps32, 0, sizeof(float) * 6 * d.N, s.stream);
+      cudaMemsetAsync(s.cmean, 0, sizeof(double) * 6, s.stream);
+      cudaMemsetAsync(s.acc, 0, sizeof(BatchAcc), s.stream);
+      SolveState s0;
+      std::memset(&s0, 0, sizeof(s0));
+      s0.maxit = 1 << 30;
+      s0.tol = tol;
+      s0.eta = INFINITY;
+      s0.eta_min = INFINITY;
+      cudaMemcpy(s.st, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+      cudaMemcpy(s.st_in, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+    }
+    e = cudaDeviceSynchronize();
+  }
+  // capture one window of every slot as parallel branches of one graph
+  if (e == cudaSuccess) {
+    cudaEvent_t fork;
+    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    std::vector<cudaEvent_t> joins(nslots, nullptr);
+    for (int i = 0; i < nslots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaEventRecord(fork, main);
+      for (int i = 0; i < nslots; ++i) {
+        BatchSlot& s = slots[i];
+        cudaStreamWaitEvent(s.stream, fork, 0);
+        const GammaParams<double> gp64 = gamma_params<double>(s.g, sc->op, s.g->tabA, s.g->tabB);
+        const GammaParams<float> gp32 = gamma_params<float>(s.g, sc->op, s.g->tabA32, s.g->tabB32);
+        slot_window(s, gp64, gp32, tol, window);
+        cudaEventRecord(joins[i], s.stream);
+        cudaStreamWaitEvent(main, joins[i], 0);
+      }
+      batch_all_done_kernel<<<1, 256, 0, main>>>(d_sts, nslots, d_flag);
+      e = cudaStreamEndCapture(main, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaEventDestroy(fork);
+    for (auto ev : joins) if (ev) cudaEventDestroy(ev);
+  }
+  // replay until every slot has converged (or the iteration budget is spent)
+  int windows = 0;
+  const int max_windows = std::max(1, (maxit + window - 1) / window);
+  while (e == cudaSuccess && windows < max_windows) {
+    e = cudaGraphLaunch(exec, main);
+    ++windows;
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+    if (flag) break;
+  }
+  // slots still running after the budget: the last outer pass holds their best FP64 state
+  if (e == cudaSuccess) {
+    int all_done = 1;
+    for (int i = 0; i < nslots; ++i) {
+      SolveState h;
+      e = cudaMemcpy(&h, slots[i].st, sizeof(h), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      if (h.done == 0) all_done = 0;
+    }
+    if (e == cudaSuccess && !all_done) rc = GFP_ERR_NOT_CONVERGED;
+  }
+  if (e == cudaSuccess) {
+    for (int i = 0; i < count; ++i)
+      for (int J = 0; J < 6; ++J) {
+        BatchSlot& s = slots[i * 6 + J];
+        SolveState so, si;
+        BatchAcc acc;
+        cudaMemcpy(&so, s.st, sizeof(so), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&si, s.st_in, sizeof(si), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(&acc, s.acc, sizeof(acc), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) break;
+        for (int I = 0; I < 6; ++I) C_eff_out[(size_t)i * 36 + I * 6 + J] = so.T0[I] / (double)s.g->d.N;
+        if (iters_out) iters_out[i * 6 + J] = acc.inner + (so.done ? 0 : si.it);
+        if (so.done == 3 && rc == GFP_OK) rc = GFP_ERR_DIVERGED;
+        if (so.done == DONE_TIMEOUT) rc = GFP_ERR_DEVICE_TIMEOUT;
+      }
+  }
+  if (e != cudaSuccess) {
+    note_error(e, __LINE__);
+    rc = cuda_status(e);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (main) cudaStreamDestroy(main);
+  cudaFree(d_flag);
+  cudaFree(d_sts);
+  for (auto& s : slots) free_slot(s);
+  return rc;
 }
 
 }  // extern "C"

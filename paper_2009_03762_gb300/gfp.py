@@ -44,7 +44,8 @@ _lib = None
 
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
-           "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles")
+           "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
+           "gfp_solve_batch")
 
 
 def lib():
@@ -72,6 +73,7 @@ def lib():
     L.gfp_solve_noalloc.argtypes = [ip, ip, ip, dp, vp, vp, vp, ctypes.POINTER(Scheme), vp, dp, ip, vp,
                                      ctypes.POINTER(_Result), vp]
     L.gfp_tune.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
+    L.gfp_solve_batch.argtypes = [ip, vp, ctypes.POINTER(Scheme), dp, ip, vp, vp]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
     L.gfp_last_error_detail.argtypes = []
     L.gfp_last_error_detail.restype = ctypes.c_char_p
@@ -273,6 +275,21 @@ def solve(lam, mu, op="AFB_R", E=(0.01, 0, 0, 0, 0, 0), tol=1e-8, maxit=1000, di
         return r, g.strain()
     finally:
         g.close()
+
+
+def solve_batch(grids, sch, tol=1e-8, maxit=5000):
+    """Effective stiffness of several cells (Grid objects with phases set) in one graph-replayed batch.
+
+    Returns (C_eff [count, 6, 6], inner iterations [count, 6], status).
+    """
+    count = len(grids)
+    handles = (ctypes.c_void_p * count)(*[g._h.value for g in grids])
+    C = np.zeros((count, 36))
+    its = np.zeros((count, 6), dtype=np.int32)
+    rc = lib().gfp_solve_batch(count, ctypes.cast(handles, ctypes.c_void_p), ctypes.byref(sch), float(tol), int(maxit),
+                               C.ctypes.data_as(ctypes.c_void_p), its.ctypes.data_as(ctypes.c_void_p))
+    _check(rc, "gfp_solve_batch", ok=(0, -4))
+    return C.reshape(count, 6, 6), its, rc
 
 
 def solve_noalloc(lam, mu, eps, sch, E, tol=1e-8, maxit=1000, h=1.0, ref=None, stream=None):
