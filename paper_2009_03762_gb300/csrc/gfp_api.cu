@@ -57,6 +57,8 @@ __global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, S
   }
 }
 
+unsigned g_inject_tma_extra_tx = 0;
+
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap) {
   reduce_eta_kernel<<<1, 256, 0, s>>>(partials, np, st, hist, hist_cap);
 }
@@ -1043,6 +1045,12 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 extern "C" {
 
 const char* gfp_last_error_detail(void) { return g_detail; }
+
+int gfp_set_fault_injection(int kind, int value) {
+  if (kind != 1 || value < 0 || value > (1 << 20)) return GFP_ERR_ARG;
+  g_inject_tma_extra_tx = (unsigned)value;
+  return GFP_OK;
+}
 
 const char* gfp_error_string(int status) {
   switch (status) {

@@ -499,6 +499,9 @@ struct Passes {
 
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap);
 
+// Test-only fault injection: extra bytes the TMA z-pass barrier waits for (0 = off).
+extern unsigned g_inject_tma_extra_tx;
+
 template <typename R> int cz_cols_max(int n3);
 template <typename R> int cy_cols_max(int n2);
 

@@ -140,7 +140,8 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
         const int ntiles = ntx * d.n2;                                                                        \
         const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \
         pass_z_tma_kernel<R, N><<<gsz, th, smt, s>>>(*reinterpret_cast<const CUtensorMap*>(lc.ztmap), spec, tw, \
-                                                      d, lc.z_cols, ntx, gp, partials, st, mode, vsrc);       \
+                                                      d, lc.z_cols, ntx, gp, partials, st, mode, vsrc,        \
+                                                      g_inject_tma_extra_tx);                                 \
         return;                                                                                               \
       }                                                                                                       \
       const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols);                                        \

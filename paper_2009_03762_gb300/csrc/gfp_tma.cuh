@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
                                                             const typename C<R>::T* __restrict__ tw, Dims d, int cols,
                                                             int ntx, GammaParams<R> gp, double* __restrict__ partials,
                                                             SolveState* __restrict__ st, int mode,
-                                                            float2* __restrict__ vsrc) {
+                                                            float2* __restrict__ vsrc, unsigned extra_tx) {
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
   const int w6 = 6 * cols;
   const int l = threadIdx.x % w6, t = threadIdx.x / w6;
   const int comp = l / cols, col = l % cols;
-  const unsigned tile_bytes = (unsigned)(tile_elems * sizeof(T));
+  // extra_tx > 0 (fault injection in tests) makes the barrier expect bytes that never arrive
+  const unsigned tile_bytes = (unsigned)(tile_elems * sizeof(T)) + extra_tx;
   constexpr int ZB = N < 256 ? N : 256;
   auto issue = [&](int tile, int b) {
     const int k2 = tile / ntx, k10 = (tile % ntx) * cols;

@@ -45,7 +45,7 @@ _lib = None
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
            "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
-           "gfp_solve_batch")
+           "gfp_solve_batch", "gfp_set_fault_injection")
 
 
 def lib():
@@ -74,6 +74,7 @@ def lib():
                                      ctypes.POINTER(_Result), vp]
     L.gfp_tune.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
     L.gfp_solve_batch.argtypes = [ip, vp, ctypes.POINTER(Scheme), dp, ip, vp, vp]
+    L.gfp_set_fault_injection.argtypes = [ip, ip]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
     L.gfp_last_error_detail.argtypes = []
     L.gfp_last_error_detail.restype = ctypes.c_char_p
@@ -180,7 +181,7 @@ class Grid:
                              ctypes.byref(r))
         if raise_on_error:
             _check(rc, "gfp_solve")
-        elif rc not in (0, -4, -5):
+        elif rc not in (0, -4, -5, -6):
             raise GfpError(rc, "gfp_solve")
         if hist is not None:
             hist = hist[:r.iters]
