@@ -104,12 +104,13 @@ __device__ __forceinline__ void cfft(T* v, SLine<T, PAD> sm, int t, const T* __r
 // ------------------------------------------------------------------------------------------------
 // pass_y: CTA = C columns of k1 x all n2 rows of one component at fixed k3; thread = (column, t).
 // ------------------------------------------------------------------------------------------------
-template <typename R, int N, bool INV>
+template <typename R, int N, bool INV, int COLS>
 __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restrict__ spec,
-                                                       const typename C<R>::T* __restrict__ tw, Dims d, int cols,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d, int cols_arg,
                                                        const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
+  const int cols = COLS > 0 ? COLS : cols_arg;
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
 #pragma unroll
     for (int r = 0; r < P::R(0); ++r) {
       T x; x.x = 0; x.y = 0;
-      if (live) x = g[(long long)cin_idx<N, 0>(t, b, r) * d.P];
+      if (live) x = g[cin_idx<N, 0>(t, b, r) * d.P];
       v[b * P::R(0) + r] = x;
     }
   __syncthreads();
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
 #pragma unroll
     for (int b = 0; b < P::E / RL; ++b)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) g[(long long)cout_idx<N, P::NST - 1>(t, b, r) * d.P] = v[b * RL + r];
+      for (int r = 0; r < RL; ++r) g[cout_idx<N, P::NST - 1>(t, b, r) * d.P] = v[b * RL + r];
   }
 }
 
@@ -149,13 +150,15 @@ template <typename R, int N> struct ZBound {
   static constexpr int blocks = (sizeof(R) == 4 && CPlan<N>::E <= 16) ? 2 : 1;
 };
 
-template <typename R, int N>
+// COLS > 0 fixes the tile width at compile time (index arithmetic folds); COLS = 0 reads cols_arg.
+template <typename R, int N, int COLS>
 __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
-                                                       const typename C<R>::T* __restrict__ tw, Dims d, int cols,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d, int cols_arg,
                                                        GammaParams<R> gp, double* __restrict__ partials,
                                                        SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
+  const int cols = COLS > 0 ? COLS : cols_arg;
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   const int k2 = blockIdx.y;
   const bool live = k10 + col < d.n1h;
   T* g = spec + comp * d.S + (long long)k2 * d.P + k10 + col;
-  const long long zs = (long long)d.n2 * d.P;
+  const int zs = d.n2 * d.P;  // row stride of one component; N zs < 2^31 for every supported grid
   T v[P::E];
 #pragma unroll
   for (int b = 0; b < P::E / P::R(0); ++b)

@@ -18,9 +18,12 @@ cudaError_t Passes<R>::setup() {
 #define GFP_SET(N)                                                                                          \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_x_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_x_a_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   GFP_FOR_CSIZES(GFP_SET)
 #undef GFP_SET
 #define GFP_SET_TMA(N) \
@@ -112,8 +115,11 @@ void Passes<R>::pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spe
     case N: {                                                                                       \
       const size_t smc = sizeof(T) * (size_t)(N + N * lc.y_cols);                                   \
       const int th = lc.y_cols * CPlan<N>::T;                                                       \
-      if (inverse) pass_y_c_kernel<R, N, true><<<grid, th, smc, s>>>(spec, tw, d, lc.y_cols, st);   \
-      else pass_y_c_kernel<R, N, false><<<grid, th, smc, s>>>(spec, tw, d, lc.y_cols, st);          \
+      if (lc.y_cols == 16) {                                                                        \
+        if (inverse) pass_y_c_kernel<R, N, true, 16><<<grid, th, smc, s>>>(spec, tw, d, 16, st);    \
+        else pass_y_c_kernel<R, N, false, 16><<<grid, th, smc, s>>>(spec, tw, d, 16, st);           \
+      } else if (inverse) pass_y_c_kernel<R, N, true, 0><<<grid, th, smc, s>>>(spec, tw, d, lc.y_cols, st); \
+      else pass_y_c_kernel<R, N, false, 0><<<grid, th, smc, s>>>(spec, tw, d, lc.y_cols, st);       \
       return;                                                                                       \
     }
     GFP_FOR_CSIZES(GFP_CASE)
@@ -145,7 +151,10 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
         return;                                                                                               \
       }                                                                                                       \
       const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols);                                        \
-      pass_z_c_kernel<R, N><<<grid, th, smc, s>>>(spec, tw, d, lc.z_cols, gp, partials, st, mode, vsrc);      \
+      if (lc.z_cols == 4)                                                                                     \
+        pass_z_c_kernel<R, N, 4><<<grid, th, smc, s>>>(spec, tw, d, 4, gp, partials, st, mode, vsrc);         \
+      else                                                                                                    \
+        pass_z_c_kernel<R, N, 0><<<grid, th, smc, s>>>(spec, tw, d, lc.z_cols, gp, partials, st, mode, vsrc); \
       return;                                                                                                 \
     }
     GFP_FOR_CSIZES(GFP_CASE)
