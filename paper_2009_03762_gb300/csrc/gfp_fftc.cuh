@@ -59,6 +59,16 @@ __device__ __forceinline__ void cstage(T* v, int t, const T* __restrict__ tw) {
   }
 }
 
+// 16-byte asynchronous global -> shared copies (L2 only) and a full wait.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Line buffer in shared memory with an element stride and an optional pad of one element per 16
 // (line-major buffers, to spread the strided Stockham writes over the banks).
 template <typename T, bool PAD>
@@ -173,6 +183,18 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   const bool live = k10 + col < d.n1h;
   T* g = spec + comp * d.S + (long long)k2 * d.P + k10 + col;
   const int zs = d.n2 * d.P;  // row stride of one component; N zs < 2^31 for every supported grid
+  // inner iterations: stage this tile's FP64-residual source [3][N][cols] while the transform runs
+  float2* vs = reinterpret_cast<float2*>(buf + 6 * N * cols);
+  // (2 or 4 columns: 16-byte granules, and the padded row pitch P, a multiple of 4, covers the last chunk)
+  const bool stage_v = (mode == PZ_INNER) && (cols == 2 || cols == 4);
+  if (stage_v) {
+    const int per_row = cols / 2;  // 16-byte granules per row
+    for (int i = threadIdx.x; i < 3 * N * per_row; i += blockDim.x) {
+      const int gr = i % per_row, rz = i / per_row;
+      const int z = rz % N, c = rz / N;
+      cp_async16(vs + (c * N + z) * cols + 2 * gr, vsrc + c * d.S + ((long long)z * d.n2 + k2) * d.P + k10 + 2 * gr);
+    }
+  }
   T v[P::E];
 #pragma unroll
   for (int b = 0; b < P::E / P::R(0); ++b)
@@ -190,6 +212,7 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   for (int b = 0; b < P::E / RL; ++b)
 #pragma unroll
     for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  if (stage_v) cp_async_wait_all();
   __syncthreads();
   // Green operator, residual and T(0) per (k3, column)
   R acc = 0;
@@ -216,7 +239,9 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
     T v1, v2, v3;
     tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
     if (mode == PZ_INNER) {
-      const float2 s1 = vsrc[vi], s2 = vsrc[d.S + vi], s3 = vsrc[2 * d.S + vi];
+      float2 s1, s2, s3;
+      if (stage_v) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
+      else { s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi]; }
       v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
     }
     R r2 = vnorm2(v1, v2, v3);
@@ -425,14 +450,6 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
 // at once, then runs the same transform / update / stress / transform sequence as pass_x_c_kernel
 // from shared memory.  Meant for small CTAs (few lines), several resident per SM.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
-               "l"(gsrc)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
 
 template <typename R, int N>
 __host__ __device__ constexpr int xa_spec_pitch() {  // complex elements per staged spectrum row (16-byte multiple)

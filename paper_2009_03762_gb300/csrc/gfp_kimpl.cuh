@@ -150,7 +150,8 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
                                                       g_inject_tma_extra_tx);                                 \
         return;                                                                                               \
       }                                                                                                       \
-      const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols);                                        \
+      const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols) +                                       \
+                         (mode == PZ_INNER && (lc.z_cols == 2 || lc.z_cols == 4) ? sizeof(float2) * 3 * N * lc.z_cols : 0);     \
       if (lc.z_cols == 4)                                                                                     \
         pass_z_c_kernel<R, N, 4><<<grid, th, smc, s>>>(spec, tw, d, 4, gp, partials, st, mode, vsrc);         \
       else                                                                                                    \
