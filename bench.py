@@ -252,6 +252,34 @@ def passes_only(args):
     return out
 
 
+def convergence_experiment(args):
+    """Iterations to eta < tol versus phase contrast for the paper's 3D matrix-inclusion cell (Sec. 6):
+    sharp cube of edge n/2 by voxel index, lambda_M = mu_M = 0.6, chi = lambda_I/lambda_M = mu_I/mu_M,
+    mean strain E_xy = 1; reference medium C_H = C_I (the paper's, chi > 1 only) or 1/2 (min + max).
+    F runs in FP64; ACD and AFB/R in mixed precision (same iterates up to the FP32 inner accuracy)."""
+    import torch
+    from paper_2009_03762_gb300 import gfp, microstructure as M
+    n = args.n
+    ind = M.cube_indicator(n, n // 2)
+    out = []
+    g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
+    for chi in (1e-3, 1e-2, 1e-1, 10.0, 1e2, 1e3):
+        lam = 0.6 * (1.0 + ind * (chi - 1.0))
+        mu = lam.copy()
+        refs = [("mean", None)] + ([("C_I", (0.6 * chi, 0.6 * chi))] if chi > 1 else [])
+        for ref_name, ref in refs:
+            g.set_phases(lam, mu, ref)
+            for op, prec, maxit in (("F", "FP64", args.conv_maxit_f), ("ACD", "MIXED", 20000), ("AFB_R", "MIXED", 20000)):
+                t0 = time.perf_counter()
+                r = g.solve(gfp.scheme(op, "TD", prec), [0, 0, 0, 0, 0, 1.0], args.conv_tol, maxit)
+                out.append({"chi": chi, "ref": ref_name, "scheme": op, "precision": prec, "iters": r.iters,
+                            "status": gfp.STATUS[r.status], "residual": r.residual, "seconds": time.perf_counter() - t0,
+                            "sigma_xy": float(r.sigma_mean[5])})
+                print(json.dumps(out[-1]), flush=True)
+    g.close()
+    return out
+
+
 def oracle_sample(n, op, iters):
     """Time the FP64 oracle as it stands on `iters` iterations of the same workload."""
     from oracle import gfp_oracle as O
@@ -282,6 +310,9 @@ def main():
     ap.add_argument("--ttt-maxit", type=int, default=3000)
     ap.add_argument("--tune", type=int, default=1, help="run the tile autotuner before timing")
     ap.add_argument("--tiles", default="", help="x lines,y columns,z columns (negative z: TMA z-pass)")
+    ap.add_argument("--experiment", default="", help="conv3d: iterations vs contrast for the paper's 3D cell")
+    ap.add_argument("--conv-tol", type=float, default=1e-8)
+    ap.add_argument("--conv-maxit-f", type=int, default=3000)
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--passes-only", type=int, default=0,
@@ -309,6 +340,9 @@ def main():
         return
     if args.passes_only:
         print(json.dumps(passes_only(args)))
+        return
+    if args.experiment == "conv3d":
+        convergence_experiment(args)
         return
     rank, world, local = dist_setup()
     line = run_gfp(args, rank, world, local)
