@@ -23,15 +23,29 @@ namespace gfp {
 __global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, SolveState* st, double* hist,
                                   int hist_cap) {
   if (st->done) return;
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
+  __shared__ double sh[32];
+  // four independent partial sums per thread keep four L2 loads in flight (a single running sum
+  // serialises one load latency per partial)
+  const int step = blockDim.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = threadIdx.x;
+  for (; i + 3 * step < np; i += 4 * step) {
+    s0 += partials[i];
+    s1 += partials[i + step];
+    s2 += partials[i + 2 * step];
+    s3 += partials[i + 3 * step];
   }
+  for (; i < np; i += step) s0 += partials[i];
+  double s = (s0 + s1) + (s2 + s3);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) sh[0] = s;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double* t = st->T0;
     const double t0 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + 2.0 * (t[3] * t[3] + t[4] * t[4] + t[5] * t[5]);
@@ -60,7 +74,7 @@ __global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, S
 unsigned g_inject_tma_extra_tx = 0;
 
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap) {
-  reduce_eta_kernel<<<1, 256, 0, s>>>(partials, np, st, hist, hist_cap);
+  reduce_eta_kernel<<<1, 1024, 0, s>>>(partials, np, st, hist, hist_cap);
 }
 
 __global__ void fill_eps_kernel(double* eps, long long N, double e0, double e1, double e2, double e3, double e4,
@@ -200,7 +214,7 @@ __global__ void dgo_table_kernel(double* __restrict__ tab, Dims d, const double*
     auto s2 = [&](int a, int b) { return S2[c_mono2[a][b]]; };
     auto dl = [](int a, int b) { return a == b ? 1.0 : 0.0; };
     const long long S = d.S;
-    const long long pos = ((long long)o3 * d.n2 + o2) * d.P + o1;
+    const long long pos = d.row(o3, o2) * d.P + o1;
     int q = 0;
     for (int P = 0; P < 6; ++P)
       for (int Q = P; Q < 6; ++Q, ++q) {
@@ -1540,7 +1554,7 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
   };
   const int ycmax = mixed ? cy_cols_max<float>(d.n2) : cy_cols_max<double>(d.n2);
-  const int zcmax = mixed ? cz_cols_max<float>(d.n3) : cz_cols_max<double>(d.n3);
+  auto zc_ok = [&](int cc) { return mixed ? cz_cols_ok<float>(d.n3, cc) : cz_cols_ok<double>(d.n3, cc); };
   // x-pass lines (register-FFT sizes only)
   {
     const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
@@ -1577,7 +1591,7 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     float bt = run(2, lc);
     CUtensorMap cand_map;
     for (int cc : cands) {
-      if (cc > zcmax || cc > d.n1h || (long long)(d.n3 + 12 * cc * d.n3) * eb > budget) continue;
+      if (!zc_ok(cc) || cc > d.n1h || (long long)(d.n3 + 12 * cc * d.n3) * eb > budget) continue;
       for (int use_tma = 0; use_tma < 2; ++use_tma) {
         LaunchCfg c = lc;
         c.z_cols = cc;
@@ -1615,11 +1629,11 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   const int eb = mixed ? 8 : 16;
   const long long budget = 200 * 1024;
   const int ycmax = mixed ? cy_cols_max<float>(d.n2) : cy_cols_max<double>(d.n2);
-  const int zcmax = mixed ? cz_cols_max<float>(d.n3) : cz_cols_max<double>(d.n3);
   const int zc = tiles[2] < 0 ? -tiles[2] : tiles[2];
+  const bool zc_ok = mixed ? cz_cols_ok<float>(d.n3, zc) : cz_cols_ok<double>(d.n3, zc);
   const int xl = tiles[0] < 0 ? -tiles[0] : tiles[0];
   if (xl > 16 || tiles[1] < 1 || tiles[1] > ycmax || tiles[1] > d.n1h || zc < 1 ||
-      zc > zcmax || zc > d.n1h || (long long)(d.n2 + 2 * tiles[1] * d.n2) * eb > budget ||
+      !zc_ok || zc > d.n1h || (long long)(d.n2 + 2 * tiles[1] * d.n2) * eb > budget ||
       (long long)(d.n3 + 12 * zc * d.n3) * eb > budget)
     return GFP_ERR_ARG;
   LaunchCfg& lc = mixed ? g->lc32 : g->lc64;

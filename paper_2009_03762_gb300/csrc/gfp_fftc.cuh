@@ -129,14 +129,15 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
   const int col = threadIdx.x % cols, t = threadIdx.x / cols;
   const int k1 = blockIdx.x * cols + col;
   const bool live = k1 < d.n1h;
-  T* g = spec + blockIdx.z * d.S + (long long)blockIdx.y * d.n2 * d.P + k1;
+  T* g = spec + blockIdx.z * d.S + d.row(blockIdx.y, 0) * d.P + k1;
+  const int ys = d.ystride();
   T v[P::E];
 #pragma unroll
   for (int b = 0; b < P::E / P::R(0); ++b)
 #pragma unroll
     for (int r = 0; r < P::R(0); ++r) {
       T x; x.x = 0; x.y = 0;
-      if (live) x = g[cin_idx<N, 0>(t, b, r) * d.P];
+      if (live) x = g[cin_idx<N, 0>(t, b, r) * ys];
       v[b * P::R(0) + r] = x;
     }
   __syncthreads();
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
 #pragma unroll
     for (int b = 0; b < P::E / RL; ++b)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) g[cout_idx<N, P::NST - 1>(t, b, r) * d.P] = v[b * RL + r];
+      for (int r = 0; r < RL; ++r) g[cout_idx<N, P::NST - 1>(t, b, r) * ys] = v[b * RL + r];
   }
 }
 
@@ -154,15 +155,18 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
 // pass_z_gamma: CTA = C columns x 6 components x all n3 rows at fixed k2; line = (comp, col).
 // Same modes as the generic kernel (PZ_GAMMA, PZ_RESIDUAL, PZ_INNER).
 // ------------------------------------------------------------------------------------------------
-// FP32 register FFTs of up to 16 elements per thread fit two 384-thread CTAs per SM.
-template <typename R, int N> struct ZBound {
-  static constexpr int threads = (sizeof(R) == 4 && CPlan<N>::E <= 16) ? 384 : 512;
-  static constexpr int blocks = (sizeof(R) == 4 && CPlan<N>::E <= 16) ? 2 : 1;
+// FP32 register FFTs of up to 16 elements per thread fit two 384-thread CTAs per SM, or one
+// 768-thread CTA for 8-column tiles (64-byte row segments, twice the DRAM efficiency of 32-byte
+// segments on the 6-component z-columns).
+template <typename R, int N, int COLS = 0> struct ZBound {
+  static constexpr bool small = sizeof(R) == 4 && CPlan<N>::E <= 16;
+  static constexpr int threads = small ? (COLS == 8 ? 768 : 384) : 512;
+  static constexpr int blocks = small ? (COLS == 8 ? 1 : 2) : 1;
 };
 
 // COLS > 0 fixes the tile width at compile time (index arithmetic folds); COLS = 0 reads cols_arg.
 template <typename R, int N, int COLS>
-__global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
+__global__ void __launch_bounds__(ZBound<R, N, COLS>::threads, ZBound<R, N, COLS>::blocks) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
                                                        const typename C<R>::T* __restrict__ tw, Dims d, int cols_arg,
                                                        GammaParams<R> gp, double* __restrict__ partials,
                                                        SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
@@ -172,27 +176,41 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
-  T* buf = twl + N;                          // [k3][6][cols]
+  T* ab3 = twl + N;                          // (A_3, B_3) per k3
+  T* buf = ab3 + N;                          // [k3][ZS]: 6 components x cols, then cols of padding
+  // Row pitch 7 cols: with 8-byte elements each half-warp of the Green step (4 or 8 rows x cols
+  // columns of one component) then touches every bank once.
+  const int ZS = 7 * cols;
   __shared__ double red[32];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    twl[i] = tw[i];
+    T ab;
+    ab.x = gp.A[2][i];
+    ab.y = gp.B[2][i];
+    ab3[i] = ab;
+  }
   const int w6 = 6 * cols;
   const int l = threadIdx.x % w6, t = threadIdx.x / w6;
   const int comp = l / cols, col = l % cols;
   const int k10 = blockIdx.x * cols;
   const int k2 = blockIdx.y;
   const bool live = k10 + col < d.n1h;
-  T* g = spec + comp * d.S + (long long)k2 * d.P + k10 + col;
-  const int zs = d.n2 * d.P;  // row stride of one component; N zs < 2^31 for every supported grid
+  T* g = spec + comp * d.S + d.row(0, k2) * d.P + k10 + col;
+  const int zs = (int)d.zstride();  // N zs < 2^31 for every supported grid
   // inner iterations: stage this tile's FP64-residual source [3][N][cols] while the transform runs
-  float2* vs = reinterpret_cast<float2*>(buf + 6 * N * cols);
-  // (2 or 4 columns: 16-byte granules, and the padded row pitch P, a multiple of 4, covers the last chunk)
-  const bool stage_v = (mode == PZ_INNER) && (cols == 2 || cols == 4);
+  float2* vs = reinterpret_cast<float2*>(buf + ZS * N);
+  // (2, 4 or 8 columns in 16-byte granules of two columns.  The row pitch P is a multiple of 4, so a
+  // granule lies wholly inside or wholly beyond the row; granules at or beyond P are not copied (an
+  // 8-column tile can reach past P, and past the end of the buffer on its last row), and the
+  // columns they would hold are never read.)
+  const bool stage_v = (mode == PZ_INNER) && (cols == 2 || cols == 4 || cols == 8);
   if (stage_v) {
     const int per_row = cols / 2;  // 16-byte granules per row
     for (int i = threadIdx.x; i < 3 * N * per_row; i += blockDim.x) {
       const int gr = i % per_row, rz = i / per_row;
       const int z = rz % N, c = rz / N;
-      cp_async16(vs + (c * N + z) * cols + 2 * gr, vsrc + c * d.S + ((long long)z * d.n2 + k2) * d.P + k10 + 2 * gr);
+      if (k10 + 2 * gr >= d.P) continue;
+      cp_async16(vs + (c * N + z) * cols + 2 * gr, vsrc + c * d.S + d.row(z, k2) * d.P + k10 + 2 * gr);
     }
   }
   T v[P::E];
@@ -205,7 +223,7 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
       v[b * P::R(0) + r] = x;
     }
   __syncthreads();
-  const SLine<T, false> sl{buf + l, w6};
+  const SLine<T, false> sl{buf + l, ZS};
   cfft<N, false>(v, sl, t, twl);
   constexpr int RL = P::R(P::NST - 1);
 #pragma unroll
@@ -214,65 +232,70 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
     for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
   if (stage_v) cp_async_wait_all();
   __syncthreads();
-  // Green operator, residual and T(0) per (k3, column)
+  // Green operator, residual and T(0) per (k3, column).  blockDim.x = 6 cols T, so every thread
+  // keeps one column and steps through k3.
   R acc = 0;
   const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
   const R b2 = gp.B[1][k2], a2 = gp.A[1][k2];
-  for (int i = threadIdx.x; i < N * cols; i += blockDim.x) {
-    const int cc = i % cols, z = i / cols;
-    const int k1 = k10 + cc;
-    if (k1 >= d.n1h) continue;
-    T tt[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) tt[c] = buf[(z * 6 + c) * cols + cc];
+  const int cc = threadIdx.x % cols;
+  const int k1 = k10 + cc;
+  if (k1 < d.n1h) {
     const R a1 = gp.A[0][k1], b1 = gp.B[0][k1];
-    const R a3 = gp.A[2][z], b3 = gp.B[2][z];
-    const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
     const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
-    const bool ny3 = (2 * z == N);
     const bool self1 = (k1 == 0) || ny1;
-    const long long vi = ((long long)z * d.n2 + k2) * d.P + k1;
-    if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
+    const int zstep = blockDim.x / cols;
+    for (int z = threadIdx.x / cols; z < N; z += zstep) {
+      T* row = buf + z * ZS + cc;
+      T tt[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
-    }
-    T v1, v2, v3;
-    tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
-    if (mode == PZ_INNER) {
-      float2 s1, s2, s3;
-      if (stage_v) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
-      else { s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi]; }
-      v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
-    }
-    R r2 = vnorm2(v1, v2, v3);
-    if (!self1) {
-      if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(tt, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
-      else r2 *= (R)2;
-    }
-    acc += r2;
-    if (mode == PZ_RESIDUAL) {
-      float2 o1, o2, o3;
-      o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
-      o3.x = (float)v3.x; o3.y = (float)v3.y;
-      vsrc[vi] = o1; vsrc[d.S + vi] = o2; vsrc[2 * d.S + vi] = o3;
-      continue;
-    }
-    T o[6];
-    if (mode == PZ_DGO) {
-      dgo_apply_point<R>(tt, gp.dgo, vi, d.S, gp.invN, o);
+      for (int c = 0; c < 6; ++c) tt[c] = row[c * cols];
+      const T ab = ab3[z];
+      const R a3 = ab.x, b3 = ab.y;
+      const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
+      const bool ny3 = (2 * z == N);
+      const long long vi = d.row(z, k2) * d.P + k1;
+      if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
-      continue;
-    }
-    gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
-    if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
-      T o2[6];
-      gamma0_apply<R>(tt, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
+        for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
+      }
+      T v1, v2, v3;
+      tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
+      if (mode == PZ_INNER) {
+        float2 s1, s2, s3;
+        if (stage_v) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
+        else { s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi]; }
+        v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
+      }
+      R r2 = vnorm2(v1, v2, v3);
+      if (!self1) {
+        if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(tt, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
+        else r2 *= (R)2;
+      }
+      acc += r2;
+      if (mode == PZ_RESIDUAL) {
+        float2 o1, o2, o3;
+        o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
+        o3.x = (float)v3.x; o3.y = (float)v3.y;
+        vsrc[vi] = o1; vsrc[d.S + vi] = o2; vsrc[2 * d.S + vi] = o3;
+        continue;
+      }
+      T o[6];
+      if (mode == PZ_DGO) {
+        dgo_apply_point<R>(tt, gp.dgo, vi, d.S, gp.invN, o);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
-    }
+        for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
+        continue;
+      }
+      gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
+      if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
+        T o2[6];
+        gamma0_apply<R>(tt, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+        for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
+    }
   }
   double accd = (double)acc;
   for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
@@ -331,8 +354,8 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
   const SLine<T, true> sl{buf + fl * LP, 1};
   T v[P::E];
   if (have_delta) {
-    const T* A = spec + (2 * p) * d.S + li * d.P;
-    const T* B = spec + (2 * p + 1) * d.S + li * d.P;
+    const T* A = spec + (2 * p) * d.S + d.xrow(li) * d.P;
+    const T* B = spec + (2 * p + 1) * d.S + d.xrow(li) * d.P;
 #pragma unroll
     for (int b = 0; b < P::E / P::R(0); ++b)
 #pragma unroll
@@ -438,7 +461,7 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
     T A, B;
     A.x = (R)0.5 * (zk.x + zn.x); A.y = (R)0.5 * (zk.y - zn.y);
     B.x = (R)0.5 * (zk.y + zn.y); B.y = (R)-0.5 * (zk.x - zn.x);
-    const long long row = lj * d.P;
+    const long long row = d.xrow(lj) * d.P;
     spec[(2 * q) * d.S + row + k] = A;
     spec[(2 * q + 1) * d.S + row + k] = B;
   }
@@ -498,7 +521,7 @@ __global__ void __launch_bounds__(512) pass_x_a_kernel(typename C<R>::T* __restr
         const long long li = line0 + l;
         if (li >= nlines) continue;
         cp_async16(reinterpret_cast<unsigned char*>(sspec + (c * lines + l) * SP) + 16 * ch,
-                   reinterpret_cast<const unsigned char*>(spec + c * d.S + li * d.P) + 16 * ch);
+                   reinterpret_cast<const unsigned char*>(spec + c * d.S + d.xrow(li) * d.P) + 16 * ch);
       } else {
         const int j = i - nsp;
         const int ch = j % row_chunks, ql = j / row_chunks;
@@ -610,7 +633,7 @@ __global__ void __launch_bounds__(512) pass_x_a_kernel(typename C<R>::T* __restr
     T A, B;
     A.x = (R)0.5 * (zk.x + zn.x); A.y = (R)0.5 * (zk.y - zn.y);
     B.x = (R)0.5 * (zk.y + zn.y); B.y = (R)-0.5 * (zk.x - zn.x);
-    const long long row = lj * d.P;
+    const long long row = d.xrow(lj) * d.P;
     spec[(2 * q) * d.S + row + k] = A;
     spec[(2 * q + 1) * d.S + row + k] = B;
   }

@@ -2,6 +2,6 @@
 #include "gfp_kimpl.cuh"
 namespace gfp {
 template struct Passes<float>;
-template int cz_cols_max<float>(int);
+template bool cz_cols_ok<float>(int, int);
 template int cy_cols_max<float>(int);
 }

@@ -2,6 +2,6 @@
 #include "gfp_kimpl.cuh"
 namespace gfp {
 template struct Passes<double>;
-template int cz_cols_max<double>(int);
+template bool cz_cols_ok<double>(int, int);
 template int cy_cols_max<double>(int);
 }

@@ -23,6 +23,13 @@ struct Dims {
   int P;        // spectrum row pitch (complex elements)
   long long N;  // n1 n2 n3
   long long S;  // spectrum component stride = n3 n2 P
+  // Spectrum rows are ordered (k3, k2), k2 fastest, like the real-space x-lines li = i3 n2 + i2: the
+  // x-pass then reads and writes whole runs of consecutive rows.  (The transposed order (k2, k3)
+  // makes the Green pass's z-columns contiguous but slows the x-pass by more than it gains.)
+  __host__ __device__ long long row(int k3, int k2) const { return (long long)k3 * n2 + k2; }
+  __host__ __device__ long long xrow(long long li) const { return li; }
+  __host__ __device__ int ystride() const { return P; }                        // elements between k2 and k2 + 1
+  __host__ __device__ long long zstride() const { return (long long)n2 * P; }  // elements between k3 and k3 + 1
 };
 
 // SolveState::done values besides 0 (running): 1 converged, 2 maxit, 3 diverged, DONE_TIMEOUT when a
@@ -97,6 +104,11 @@ __device__ __forceinline__ void tk_vec(const T t[6], R k1, R k2, R k3, T& v1, T&
   v3.x = t[4].x * k1 + t[3].x * k2 + t[2].x * k3;  v3.y = t[4].y * k1 + t[3].y * k2 + t[2].y * k3;
 }
 
+// 1 / |kt|^2 for the Green operator: exact in FP64; in FP32 (only the inner correction iterations,
+// whose result the FP64 residual pass re-checks) the hardware reciprocal, within 2 ulp.
+__device__ __forceinline__ double recip_gamma(double s) { return 1.0 / s; }
+__device__ __forceinline__ float recip_gamma(float s) { return __fdividef(1.0f, s); }
+
 // Real isotropic Gamma0(kt) applied to a tensor whose product with kt is v, times -scale:
 // out_ij = -scale [ (k_i v_j + k_j v_i) / (2 mu s) - c_lm k_i k_j (k.v) / s^2 ],  s = |kt|^2;
 // out = 0 where kt = 0 (k = 0 and the modes where the scheme's wave vector vanishes).
@@ -108,7 +120,7 @@ __device__ __forceinline__ void gamma0_from_v(T v1, T v2, T v3, R k1, R k2, R k3
     for (int c = 0; c < 6; ++c) { out[c].x = 0; out[c].y = 0; }
     return;
   }
-  const R is = (R)1 / s;
+  const R is = recip_gamma(s);
   const R a = c_mu * is * scale;               // scale / (2 mu s)
   T kv; kv.x = k1 * v1.x + k2 * v2.x + k3 * v3.x; kv.y = k1 * v1.y + k2 * v2.y + k3 * v3.y;
   const R b = c_lm * is * is * scale;
@@ -231,7 +243,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
       const long long li = line0 + l;
       T z0, z1;
       if (li < nlines) {
-        const long long row = li * d.P;        // (i3 n2 + i2) P
+        const long long row = d.xrow(li) * d.P;
         T A = spec[(2 * p) * d.S + row + k];
         T B = spec[(2 * p + 1) * d.S + row + k];
         const bool selfconj = (k == 0) || (2 * k == n1);
@@ -318,7 +330,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
     T A, B;
     A.x = (R)0.5 * (zk.x + zn.x); A.y = (R)0.5 * (zk.y - zn.y);
     B.x = (R)0.5 * (zk.y + zn.y); B.y = (R)-0.5 * (zk.x - zn.x);
-    const long long row = li * d.P;
+    const long long row = d.xrow(li) * d.P;
     spec[(2 * p) * d.S + row + k] = A;
     spec[(2 * p + 1) * d.S + row + k] = B;
   }
@@ -340,18 +352,19 @@ __global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typenam
   const int k3 = blockIdx.y;
   const int c = blockIdx.z;
   for (int i = threadIdx.x; i < d.n2; i += blockDim.x) twl[i] = tw[i];
-  T* g = spec + c * d.S + (long long)k3 * d.n2 * d.P + k10;
+  T* g = spec + c * d.S + d.row(k3, 0) * d.P + k10;
+  const long long ys = d.ystride();
   for (int i = threadIdx.x; i < d.n2 * cols; i += blockDim.x) {
     const int cc = i % cols, y = i / cols;
     T v; v.x = 0; v.y = 0;
-    if (k10 + cc < d.n1h) v = g[(long long)y * d.P + cc];
+    if (k10 + cc < d.n1h) v = g[(long long)y * ys + cc];
     buf[i] = v;
   }
   __syncthreads();
   buf = fft_lines<INV>(buf, buf2, twl, plan, LineLayout{cols, cols, 1, true});
   for (int i = threadIdx.x; i < d.n2 * cols; i += blockDim.x) {
     const int cc = i % cols, y = i / cols;
-    if (k10 + cc < d.n1h) g[(long long)y * d.P + cc] = buf[i];
+    if (k10 + cc < d.n1h) g[(long long)y * ys + cc] = buf[i];
   }
 }
 
@@ -384,7 +397,7 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
     const int cc = i % cols, rest = i / cols;
     const int comp = rest % 6, z = rest / 6;
     T v; v.x = 0; v.y = 0;
-    if (k10 + cc < d.n1h) v = spec[comp * d.S + ((long long)z * d.n2 + k2) * d.P + k10 + cc];
+    if (k10 + cc < d.n1h) v = spec[comp * d.S + d.row(z, k2) * d.P + k10 + cc];
     buf[i] = v;
   }
   __syncthreads();
@@ -407,7 +420,7 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
     const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
     const bool ny3 = ((d.n3 & 1) == 0) && (2 * z == d.n3);
     const bool self1 = (k1 == 0) || ny1;
-    const long long vi = ((long long)z * d.n2 + k2) * d.P + k1;
+    const long long vi = d.row(z, k2) * d.P + k1;
     if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) st->T0[c] = (double)t[c].x;
@@ -466,7 +479,7 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
   for (int i = threadIdx.x; i < d.n3 * w6; i += blockDim.x) {
     const int cc = i % cols, rest = i / cols;
     const int comp = rest % 6, z = rest / 6;
-    if (k10 + cc < d.n1h) spec[comp * d.S + ((long long)z * d.n2 + k2) * d.P + k10 + cc] = buf[i];
+    if (k10 + cc < d.n1h) spec[comp * d.S + d.row(z, k2) * d.P + k10 + cc] = buf[i];
   }
 }
 
@@ -502,7 +515,7 @@ void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveStat
 // Test-only fault injection: extra bytes the TMA z-pass barrier waits for (0 = off).
 extern unsigned g_inject_tma_extra_tx;
 
-template <typename R> int cz_cols_max(int n3);
+template <typename R> bool cz_cols_ok(int n3, int cols);
 template <typename R> int cy_cols_max(int n2);
 
 }  // namespace gfp

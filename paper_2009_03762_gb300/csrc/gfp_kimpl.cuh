@@ -23,7 +23,8 @@ cudaError_t Passes<R>::setup() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   GFP_FOR_CSIZES(GFP_SET)
 #undef GFP_SET
 #define GFP_SET_TMA(N) \
@@ -150,9 +151,12 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
                                                       g_inject_tma_extra_tx);                                 \
         return;                                                                                               \
       }                                                                                                       \
-      const size_t smc = sizeof(T) * (size_t)(N + 6 * N * lc.z_cols) +                                       \
-                         (mode == PZ_INNER && (lc.z_cols == 2 || lc.z_cols == 4) ? sizeof(float2) * 3 * N * lc.z_cols : 0);     \
-      if (lc.z_cols == 4)                                                                                     \
+      const size_t smc = sizeof(T) * (size_t)(2 * N + 7 * N * lc.z_cols) +                                   \
+                         (mode == PZ_INNER && (lc.z_cols == 2 || lc.z_cols == 4 || lc.z_cols == 8)                    \
+                              ? sizeof(float2) * 3 * N * lc.z_cols : 0);                                      \
+      if (lc.z_cols == 8)                                                                                     \
+        pass_z_c_kernel<R, N, 8><<<grid, th, smc, s>>>(spec, tw, d, 8, gp, partials, st, mode, vsrc);         \
+      else if (lc.z_cols == 4)                                                                                \
         pass_z_c_kernel<R, N, 4><<<grid, th, smc, s>>>(spec, tw, d, 4, gp, partials, st, mode, vsrc);         \
       else                                                                                                    \
         pass_z_c_kernel<R, N, 0><<<grid, th, smc, s>>>(spec, tw, d, lc.z_cols, gp, partials, st, mode, vsrc); \
@@ -169,14 +173,18 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
 }  // namespace gfp
 
 namespace gfp {
-// Largest z-tile width (k1 columns) the register-FFT z-pass accepts for this length and precision.
-template <typename R> int cz_cols_max(int n3) {
+// Whether the z-pass accepts a tile of `cols` k1 columns for this length and precision: any width
+// up to the limit of the runtime-width kernel, and 8 where the 8-column kernel fits its launch bound.
+template <typename R> bool cz_cols_ok(int n3, int cols) {
+  if (cols < 1) return false;
   switch (n3) {
-#define GFP_CASE(N) \
-    case N: return std::max(1, ZBound<R, N>::threads / (6 * CPlan<N>::T));
+#define GFP_CASE(N)                                                                 \
+    case N:                                                                         \
+      return 6 * cols * CPlan<N>::T <= ZBound<R, N>::threads ||                     \
+             (cols == 8 && 6 * cols * CPlan<N>::T <= ZBound<R, N, 8>::threads);
     GFP_FOR_CSIZES(GFP_CASE)
 #undef GFP_CASE
-    default: return 64;
+    default: return cols <= 64;
   }
 }
 template <typename R> int cy_cols_max(int n2) {

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
       const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
       const bool ny3 = (2 * z == N);
       const bool self1 = (k1 == 0) || ny1;
-      const long long vi = ((long long)z * d.n2 + k2) * d.P + k1;
+      const long long vi = d.row(z, k2) * d.P + k1;
       if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
       __syncthreads();
       cfft<N, true>(v, sl, t, twl);
       if (live) {
-        T* g = spec + comp * d.S + (long long)k2 * d.P + k10 + col;
-        const long long zs = (long long)d.n2 * d.P;
+        T* g = spec + comp * d.S + d.row(0, k2) * d.P + k10 + col;
+        const long long zs = d.zstride();
 #pragma unroll
         for (int bb = 0; bb < P::E / RL; ++bb)
 #pragma unroll

@@ -58,3 +58,21 @@ def test_mixed_unsupported_combinations(gfp):
         with pytest.raises(gfp.GfpError) as e:
             g.solve(gfp.scheme(op, prec="MIXED"), [0.01, 0, 0, 0, 0, 0], 1e-8, 100, raise_on_error=True)
         assert e.value.code == -8
+
+
+@pytest.mark.parametrize("zcols", [8, 4, 2])
+def test_mixed_z_tile_widths_on_256_columns(gfp, zcols):
+    """z-pass tiles of 8 columns (768-thread CTA), 4 and 2 on n3 = 256 with a ragged k1 range
+    (n1/2 + 1 = 9 columns): the mixed solve matches the FP64 GPU solve."""
+    lam, mu = M.random_field(16, 8, 256, seed=5)
+    E = [0.0, 0.0, 0.0, 0.3, 0.0, 0.0]
+    g = gfp.Grid(16, 8, 256)
+    g.set_phases(lam, mu)
+    g.set_tiles(gfp.MIXED, [2, 8, zcols])
+    r = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), E, 1e-9, 20000)
+    assert r.converged and r.residual < 1e-9
+    eps = g.strain()
+    r64 = g.solve(gfp.scheme("AFB_R", "PCD", "FP64"), E, 1e-9, 20000)
+    assert r64.converged
+    assert _rel(eps, g.strain()) <= 1e-6
+    assert _rel(r.sigma_mean, r64.sigma_mean) <= 1e-6
