@@ -1599,6 +1599,7 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
         finalize_cfg(d, c);
         c.ztmap = (use_tma && encode_ztmap(&cand_map, g->spec, d, cc, mixed ? 4 : 8)) ? &cand_map : nullptr;
         if (use_tma && !c.ztmap) continue;
+        if (use_tma && !(mixed ? cz_tma_ok<float>(d.n3, cc) : cz_tma_ok<double>(d.n3, cc))) continue;
         const float t = run(2, c);
         if (t < bt) { bt = t; best = c; }
       }

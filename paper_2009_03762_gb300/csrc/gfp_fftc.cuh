@@ -155,18 +155,93 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
 // pass_z_gamma: CTA = C columns x 6 components x all n3 rows at fixed k2; line = (comp, col).
 // Same modes as the generic kernel (PZ_GAMMA, PZ_RESIDUAL, PZ_INNER).
 // ------------------------------------------------------------------------------------------------
-// FP32 register FFTs of up to 16 elements per thread fit two 384-thread CTAs per SM, or one
-// 768-thread CTA for 8-column tiles (64-byte row segments, twice the DRAM efficiency of 32-byte
-// segments on the 6-component z-columns).
-template <typename R, int N, int COLS = 0> struct ZBound {
+// FP32 register FFTs of up to 16 elements per thread fit two 384-thread CTAs per SM.
+template <typename R, int N> struct ZBound {
   static constexpr bool small = sizeof(R) == 4 && CPlan<N>::E <= 16;
-  static constexpr int threads = small ? (COLS == 8 ? 768 : 384) : 512;
-  static constexpr int blocks = small ? (COLS == 8 ? 1 : 2) : 1;
+  static constexpr int threads = small ? 384 : 512;
+  static constexpr int blocks = small ? 2 : 1;
 };
+
+// Green step on a z-tile in shared memory: rows [k3][ZS] holding 6 components x cols columns
+// (component c, column cc at c cols + cc).  Residual partial of the thread (returned), T(0), and, by
+// mode, the increment written back in place (PZ_GAMMA, PZ_INNER, PZ_DGO) or the inner-iteration
+// source stored (PZ_RESIDUAL).  vs: the tile's inner source staged as [3][N][cols], or null to read
+// it from global memory.  blockDim.x is a multiple of cols: every thread keeps one column.
+template <typename R, int N>
+__device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int ZS, int cols,
+                                        const typename C<R>::T* __restrict__ ab3, const float2* vs, const Dims& d,
+                                        int k10, int k2, const GammaParams<R>& gp, SolveState* __restrict__ st,
+                                        int mode, float2* __restrict__ vsrc) {
+  typedef typename C<R>::T T;
+  R acc = 0;
+  const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
+  const R b2 = gp.B[1][k2], a2 = gp.A[1][k2];
+  const int cc = threadIdx.x % cols;
+  const int k1 = k10 + cc;
+  if (k1 < d.n1h) {
+    const R a1 = gp.A[0][k1], b1 = gp.B[0][k1];
+    const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
+    const bool self1 = (k1 == 0) || ny1;
+    const int zstep = blockDim.x / cols;
+    for (int z = threadIdx.x / cols; z < N; z += zstep) {
+      T* row = buf + z * ZS + cc;
+      T tt[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tt[c] = row[c * cols];
+      const T ab = ab3[z];
+      const R a3 = ab.x, b3 = ab.y;
+      const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
+      const bool ny3 = (2 * z == N);
+      const long long vi = d.row(z, k2) * d.P + k1;
+      if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
+      }
+      T v1, v2, v3;
+      tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
+      if (mode == PZ_INNER) {
+        float2 s1, s2, s3;
+        if (vs) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
+        else { s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi]; }
+        v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
+      }
+      R r2 = vnorm2(v1, v2, v3);
+      if (!self1) {
+        if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(tt, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
+        else r2 *= (R)2;
+      }
+      acc += r2;
+      if (mode == PZ_RESIDUAL) {
+        float2 o1, o2, o3;
+        o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
+        o3.x = (float)v3.x; o3.y = (float)v3.y;
+        vsrc[vi] = o1; vsrc[d.S + vi] = o2; vsrc[2 * d.S + vi] = o3;
+        continue;
+      }
+      T o[6];
+      if (mode == PZ_DGO) {
+        dgo_apply_point<R>(tt, gp.dgo, vi, d.S, gp.invN, o);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
+        continue;
+      }
+      gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
+      if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
+        T o2[6];
+        gamma0_apply<R>(tt, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
+    }
+  }
+  return acc;
+}
 
 // COLS > 0 fixes the tile width at compile time (index arithmetic folds); COLS = 0 reads cols_arg.
 template <typename R, int N, int COLS>
-__global__ void __launch_bounds__(ZBound<R, N, COLS>::threads, ZBound<R, N, COLS>::blocks) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
+__global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) pass_z_c_kernel(typename C<R>::T* __restrict__ spec,
                                                        const typename C<R>::T* __restrict__ tw, Dims d, int cols_arg,
                                                        GammaParams<R> gp, double* __restrict__ partials,
                                                        SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
@@ -232,71 +307,8 @@ __global__ void __launch_bounds__(ZBound<R, N, COLS>::threads, ZBound<R, N, COLS
     for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
   if (stage_v) cp_async_wait_all();
   __syncthreads();
-  // Green operator, residual and T(0) per (k3, column).  blockDim.x = 6 cols T, so every thread
-  // keeps one column and steps through k3.
-  R acc = 0;
-  const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
-  const R b2 = gp.B[1][k2], a2 = gp.A[1][k2];
-  const int cc = threadIdx.x % cols;
-  const int k1 = k10 + cc;
-  if (k1 < d.n1h) {
-    const R a1 = gp.A[0][k1], b1 = gp.B[0][k1];
-    const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
-    const bool self1 = (k1 == 0) || ny1;
-    const int zstep = blockDim.x / cols;
-    for (int z = threadIdx.x / cols; z < N; z += zstep) {
-      T* row = buf + z * ZS + cc;
-      T tt[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) tt[c] = row[c * cols];
-      const T ab = ab3[z];
-      const R a3 = ab.x, b3 = ab.y;
-      const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
-      const bool ny3 = (2 * z == N);
-      const long long vi = d.row(z, k2) * d.P + k1;
-      if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
-      }
-      T v1, v2, v3;
-      tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
-      if (mode == PZ_INNER) {
-        float2 s1, s2, s3;
-        if (stage_v) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
-        else { s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi]; }
-        v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
-      }
-      R r2 = vnorm2(v1, v2, v3);
-      if (!self1) {
-        if (gp.nyq_avg && (ny2 || ny3)) r2 += tk_norm2<R>(tt, kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3);
-        else r2 *= (R)2;
-      }
-      acc += r2;
-      if (mode == PZ_RESIDUAL) {
-        float2 o1, o2, o3;
-        o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
-        o3.x = (float)v3.x; o3.y = (float)v3.y;
-        vsrc[vi] = o1; vsrc[d.S + vi] = o2; vsrc[2 * d.S + vi] = o3;
-        continue;
-      }
-      T o[6];
-      if (mode == PZ_DGO) {
-        dgo_apply_point<R>(tt, gp.dgo, vi, d.S, gp.invN, o);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
-        continue;
-      }
-      gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
-      if (gp.nyq_avg && (ny1 || ny2 || ny3)) {
-        T o2[6];
-        gamma0_apply<R>(tt, ny1 ? -kt1 : kt1, ny2 ? -kt2 : kt2, ny3 ? -kt3 : kt3, gp.c_mu, gp.c_lm, gp.invN, o2);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
-      }
-#pragma unroll
-      for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
-    }
-  }
+  // Green operator, residual and T(0) per (k3, column)
+  const R acc = green_tile<R, N>(buf, ZS, cols, ab3, stage_v ? vs : nullptr, d, k10, k2, gp, st, mode, vsrc);
   double accd = (double)acc;
   for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
@@ -319,6 +331,127 @@ __global__ void __launch_bounds__(ZBound<R, N, COLS>::threads, ZBound<R, N, COLS
     for (int b = 0; b < P::E / RL; ++b)
 #pragma unroll
       for (int r = 0; r < RL; ++r) g[cout_idx<N, P::NST - 1>(t, b, r) * zs] = v[b * RL + r];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass_z_gamma with 8-column tiles and two lines per thread (FP32, E <= 16): thread (l, t), l < 24,
+// transforms line l (components 0-2) from registers and line l + 24 (components 3-5), which cp.async
+// brings into the tile while line l is transformed.  The 6-component z-columns are read in 64-byte
+// row segments, which the DRAM serves about twice as fast as the 32-byte segments of 4-column tiles,
+// at the occupancy of the 4-column kernel (two CTAs of 24 T threads per SM; the unpadded tile is
+// 48 N elements).  The inner-iteration source is read from global memory in the Green step.
+// ------------------------------------------------------------------------------------------------
+template <typename R, int N>
+__global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_c2_kernel(typename C<R>::T* __restrict__ spec,
+                                                       const typename C<R>::T* __restrict__ tw, Dims d,
+                                                       GammaParams<R> gp, double* __restrict__ partials,
+                                                       SolveState* __restrict__ st, int mode, float2* __restrict__ vsrc) {
+  typedef typename C<R>::T T;
+  typedef CPlan<N> P;
+  constexpr int COLS = 8, ZS = 6 * COLS;
+  if (st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* twl = reinterpret_cast<T*>(smem_raw);
+  T* ab3 = twl + N;
+  T* buf = ab3 + N;                          // [k3][48]: component c, column cc at 8 c + cc
+  __shared__ double red[32];
+  const int k10 = blockIdx.x * COLS;
+  const int k2 = blockIdx.y;
+  // components 3-5 into the tile: 16-byte granules of two columns; the row pitch P is a multiple of
+  // 4, so granules at or beyond P (dead columns of the last tile) are skipped and never read
+  for (int i = threadIdx.x; i < 3 * N * (COLS / 2); i += blockDim.x) {
+    const int gr = i % (COLS / 2), rz = i / (COLS / 2);
+    const int z = rz % N, c = 3 + rz / N;
+    if (k10 + 2 * gr >= d.P) continue;
+    cp_async16(buf + z * ZS + c * COLS + 2 * gr, spec + c * d.S + d.row(z, k2) * d.P + k10 + 2 * gr);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    twl[i] = tw[i];
+    T ab;
+    ab.x = gp.A[2][i];
+    ab.y = gp.B[2][i];
+    ab3[i] = ab;
+  }
+  const int l = threadIdx.x % 24, t = threadIdx.x / 24;
+  const int col = l % COLS;
+  const bool live = k10 + col < d.n1h;
+  const int zs = (int)d.zstride();  // N zs < 2^31 for every supported grid
+  T* gA = spec + (l / COLS) * d.S + d.row(0, k2) * d.P + k10 + col;
+  T* gB = gA + 3 * d.S;
+  const SLine<T, false> slA{buf + l, ZS}, slB{buf + l + 24, ZS};
+  constexpr int RL = P::R(P::NST - 1);
+  T v[P::E];
+  // line A: global -> registers -> forward transform -> tile
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) {
+      T x; x.x = 0; x.y = 0;
+      if (live) x = gA[cin_idx<N, 0>(t, b, r) * zs];
+      v[b * P::R(0) + r] = x;
+    }
+  __syncthreads();
+  cfft<N, false>(v, slA, t, twl);
+#pragma unroll
+  for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) slA[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  // line B: tile -> registers -> forward transform -> tile
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) {
+      T x = slB[cin_idx<N, 0>(t, b, r)];
+      if (!live) { x.x = 0; x.y = 0; }
+      v[b * P::R(0) + r] = x;
+    }
+  __syncthreads();
+  cfft<N, false>(v, slB, t, twl);
+#pragma unroll
+  for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) slB[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
+  __syncthreads();
+  const R acc = green_tile<R, N>(buf, ZS, COLS, ab3, nullptr, d, k10, k2, gp, st, mode, vsrc);
+  double accd = (double)acc;
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+  if (mode == PZ_RESIDUAL) return;
+  // inverse transforms: tile -> registers -> global, line A then line B
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) v[b * P::R(0) + r] = slA[cin_idx<N, 0>(t, b, r)];
+  __syncthreads();
+  cfft<N, true>(v, slA, t, twl);
+  if (live) {
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) gA[cout_idx<N, P::NST - 1>(t, b, r) * zs] = v[b * RL + r];
+  }
+#pragma unroll
+  for (int b = 0; b < P::E / P::R(0); ++b)
+#pragma unroll
+    for (int r = 0; r < P::R(0); ++r) v[b * P::R(0) + r] = slB[cin_idx<N, 0>(t, b, r)];
+  __syncthreads();
+  cfft<N, true>(v, slB, t, twl);
+  if (live) {
+#pragma unroll
+    for (int b = 0; b < P::E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) gB[cout_idx<N, P::NST - 1>(t, b, r) * zs] = v[b * RL + r];
   }
 }
 

@@ -3,5 +3,6 @@
 namespace gfp {
 template struct Passes<double>;
 template bool cz_cols_ok<double>(int, int);
+template bool cz_tma_ok<double>(int, int);
 template int cy_cols_max<double>(int);
 }

@@ -516,6 +516,7 @@ void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveStat
 extern unsigned g_inject_tma_extra_tx;
 
 template <typename R> bool cz_cols_ok(int n3, int cols);
+template <typename R> bool cz_tma_ok(int n3, int cols);
 template <typename R> int cy_cols_max(int n2);
 
 }  // namespace gfp

@@ -24,7 +24,8 @@ cudaError_t Passes<R>::setup() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_y_c_kernel<R, N, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c_kernel<R, N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if constexpr (ZBound<R, N>::small)                                                                  \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_c2_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   GFP_FOR_CSIZES(GFP_SET)
 #undef GFP_SET
 #define GFP_SET_TMA(N) \
@@ -55,11 +56,17 @@ inline int tma_grid(int threads, size_t smem) {
   return sms * cached_blocks;
 }
 
+// shared memory of the compile-time x-pass for `lines` x-lines per CTA: twiddles and 3 padded
+// complex lines per x-line
+template <typename R, int N> inline size_t cx_smem_bytes(int lines) {
+  return sizeof(typename C<R>::T) * (size_t)(N + 3 * lines * (N + N / 16));
+}
 // lines per CTA of the compile-time x-pass: at most 512 threads (3 pair-lines x T each) and at most
-// 200 KB of shared memory (3 padded lines of N + N/16 elements per x-line, plus N twiddles)
+// 200 KB of shared memory
 template <typename R, int N> inline int cx_lines_max() {
   const int by_threads = 512 / (3 * CPlan<N>::T);
-  const int by_smem = (int)((200 * 1024 / sizeof(typename C<R>::T) - N) / (3 * (N + N / 16)));
+  int by_smem = 16;
+  while (by_smem > 1 && cx_smem_bytes<R, N>(by_smem) > 200 * 1024) --by_smem;
   return std::max(1, std::min(16, std::min(by_threads, by_smem)));
 }
 
@@ -81,7 +88,7 @@ inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>:
   const int lines = want_lines > 0 ? std::min(want_lines, cx_lines_max<R, N>()) : cx_lines_max<R, N>();
   const long long nlines = (long long)d.n2 * d.n3;
   const unsigned blocks = (unsigned)((nlines + lines - 1) / lines);
-  const size_t sm = sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16));
+  const size_t sm = cx_smem_bytes<R, N>(lines);
   pass_x_c_kernel<R, N><<<blocks, 3 * lines * CPlan<N>::T, sm, s>>>(spec, eps, lam, mu, tw, d, lines, flags, corr,
                                                                      corr_mean, pp, st);
 }
@@ -154,9 +161,14 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
       const size_t smc = sizeof(T) * (size_t)(2 * N + 7 * N * lc.z_cols) +                                   \
                          (mode == PZ_INNER && (lc.z_cols == 2 || lc.z_cols == 4 || lc.z_cols == 8)                    \
                               ? sizeof(float2) * 3 * N * lc.z_cols : 0);                                      \
-      if (lc.z_cols == 8)                                                                                     \
-        pass_z_c_kernel<R, N, 8><<<grid, th, smc, s>>>(spec, tw, d, 8, gp, partials, st, mode, vsrc);         \
-      else if (lc.z_cols == 4)                                                                                \
+      if constexpr (ZBound<R, N>::small) {                                                                    \
+        if (lc.z_cols == 8) {                                                                                 \
+          const size_t sm2 = sizeof(T) * (size_t)(2 * N + 48 * N);                                            \
+          pass_z_c2_kernel<R, N><<<grid, 24 * CPlan<N>::T, sm2, s>>>(spec, tw, d, gp, partials, st, mode, vsrc); \
+          return;                                                                                             \
+        }                                                                                                     \
+      }                                                                                                       \
+      if (lc.z_cols == 4)                                                                                     \
         pass_z_c_kernel<R, N, 4><<<grid, th, smc, s>>>(spec, tw, d, 4, gp, partials, st, mode, vsrc);         \
       else                                                                                                    \
         pass_z_c_kernel<R, N, 0><<<grid, th, smc, s>>>(spec, tw, d, lc.z_cols, gp, partials, st, mode, vsrc); \
@@ -174,17 +186,26 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
 
 namespace gfp {
 // Whether the z-pass accepts a tile of `cols` k1 columns for this length and precision: any width
-// up to the limit of the runtime-width kernel, and 8 where the 8-column kernel fits its launch bound.
+// up to the limit of the one-line-per-thread kernel, and 8 where the two-lines-per-thread kernel runs.
 template <typename R> bool cz_cols_ok(int n3, int cols) {
   if (cols < 1) return false;
   switch (n3) {
 #define GFP_CASE(N)                                                                 \
     case N:                                                                         \
-      return 6 * cols * CPlan<N>::T <= ZBound<R, N>::threads ||                     \
-             (cols == 8 && 6 * cols * CPlan<N>::T <= ZBound<R, N, 8>::threads);
+      return 6 * cols * CPlan<N>::T <= ZBound<R, N>::threads || (cols == 8 && ZBound<R, N>::small);
     GFP_FOR_CSIZES(GFP_CASE)
 #undef GFP_CASE
     default: return cols <= 64;
+  }
+}
+// Whether the TMA-fed z-pass can serve a tile of `cols` columns (its CTA has at most 384 threads).
+template <typename R> bool cz_tma_ok(int n3, int cols) {
+  switch (n3) {
+#define GFP_CASE(N) \
+    case N: return cols >= 1 && 6 * cols * CPlan<N>::T <= 384;
+    GFP_FOR_CSIZES(GFP_CASE)
+#undef GFP_CASE
+    default: return false;
   }
 }
 template <typename R> int cy_cols_max(int n2) {
