@@ -520,20 +520,35 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
 #pragma unroll
     for (int c = 0; c < 6; ++c) cm[c] = corr_mean[c];
   }
-  for (int i = threadIdx.x; i < lines * N; i += blockDim.x) {
+  // XU voxels per step, all their loads issued before any store: a plain loop waits one DRAM latency
+  // per voxel, since its strain loads are ordered after the previous voxel's stores to the same array
+  // (FP32: 2 voxels at 64 registers; FP64 keeps 1, its registers are already at the launch bound)
+  constexpr int XU = sizeof(R) == 4 ? 2 : 1;
+  const int nvox = lines * N;
+  for (int i0 = threadIdx.x; i0 < nvox; i0 += XU * blockDim.x) {
+    R eu[XU][6], lu[XU], mu_[XU];
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const long long lj = line0 + i / N;
+      const bool ok = i < nvox && lj < nlines;
+      const long long vv = lj * N + i % N;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) eu[u][c] = (ok && !zero) ? eps[c * d.N + vv] : (R)0;
+      lu[u] = ok ? lam[vv] : (R)0;
+      mu_[u] = ok ? mu[vv] : (R)0;
+    }
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+    const int i = i0 + u * blockDim.x;
     const int x = i % N, ll = i / N;
     const long long lj = line0 + ll;
-    if (lj >= nlines) continue;
+    if (i >= nvox || lj >= nlines) continue;
     const long long vv = lj * N + x;
     const int px = x + (x >> 4);
     R e[6];
-    if (zero) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) e[c] = (R)0;
-    } else {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) e[c] = eps[c * d.N + vv];
-    }
+    for (int c = 0; c < 6; ++c) e[c] = eu[u][c];
     if (have_delta) {
       R dd[6];
 #pragma unroll
@@ -557,10 +572,11 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
       for (int c = 0; c < 6; ++c) eps[c * d.N + vv] = e[c];
     }
     T zz[3];
-    if (polar) pack_stress<R>(e, lam[vv] - (R)pp.lam_h, mu[vv] - (R)pp.mu_h, zz);
-    else pack_stress<R>(e, lam[vv], mu[vv], zz);
+    if (polar) pack_stress<R>(e, lu[u] - (R)pp.lam_h, mu_[u] - (R)pp.mu_h, zz);
+    else pack_stress<R>(e, lu[u], mu_[u], zz);
 #pragma unroll
     for (int q = 0; q < 3; ++q) buf[(q * lines + ll) * LP + px] = zz[q];
+    }
   }
   if (polar && have_delta) {
     const double sum = block_sum(dacc, red);
