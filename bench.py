@@ -21,6 +21,33 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "voxel-iterations/s"
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture (profiles/), valid
+# only while the kernel sources hash to the value recorded with it; otherwise the traffic is unknown.
+KERNEL_SOURCES = ("gfp_fft.cuh", "gfp_fftc.cuh", "gfp_kernels.cuh", "gfp_kimpl.cuh")
+NCU_TRAFFIC = {
+    # pass_z_c2_kernel<float, 256>, 8-column z tiles, one FP32 inner iteration of the 256^3 workload
+    ("pass_z_gamma", 256, "MIXED", 8): {"bytes": 624.181504e6 + 367.726848e6,
+                                        "sources_sha1": "00c36011848f78d295c3041490ded009123dccb6"},
+}
+
+
+def kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2009_03762_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel, n, prec, tiles):
+    """Recorded DRAM traffic per launch for this kernel and configuration, or None."""
+    zc = abs(tiles[2]) if tiles else None
+    rec = NCU_TRAFFIC.get((kernel, n, prec, zc))
+    if rec is None or rec["sources_sha1"] != kernel_sources_sha1():
+        return None
+    return rec["bytes"]
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -215,7 +242,8 @@ def run_gfp(args, rank=0, world=1, local=0):
                    "l2": "inputs larger than L2 (spectrum %.0f MB)" % (6 * (8 if prec == "MIXED" else 16)
                                                                       * (n // 2 + 1) * n * n / 1e6)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(dom, n, prec, tiles),
                      "bytes_per_voxel": bpv[dom],
                      "iteration": {"achieved": it_bytes / (it_ms * 1e-3) / 1e9, "frac": it_bytes / (it_ms * 1e-3) / 1e9 / peak,
                                    "bytes_per_voxel": sum(bpv.values()), "ms": it_ms}},
