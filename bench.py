@@ -308,6 +308,52 @@ def convergence_experiment(args):
     return out
 
 
+def batch_experiment(args):
+    """Batched homogenization: random-sphere cells (n from {64, 96, 128}, volume fraction U[0.1, 0.3],
+    contrast log-uniform on [1e-2, 1e3]) x 6 Voigt loads in one graph-replayed gfp_solve_batch, mixed
+    precision to eta < 1e-8, against the same cells solved one after another (gfp_effective_stiffness).
+    Aggregate voxel-iterations/s = sum over cells and loads of N x inner iterations / wall time."""
+    import torch
+    from paper_2009_03762_gb300 import gfp, microstructure as M
+    specs = M.batch_specs(args.batch_count, seed=0)
+    sch = gfp.scheme(args.op, "PCD", "MIXED")
+    grids = []
+    tuned = {}
+    for sp in specs:
+        lam, mu = M.batch_item(sp)
+        g = gfp.Grid(sp["n"], sp["n"], sp["n"], 1.0, torch.cuda.current_stream().cuda_stream)
+        g.set_phases(lam, mu)
+        if sp["n"] not in tuned:
+            tuned[sp["n"]] = g.tune(sch)
+        else:
+            g.set_tiles(gfp.MIXED, tuned[sp["n"]])
+        grids.append(g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C, its, rc = gfp.solve_batch(grids, sch, tol=1e-8, maxit=args.batch_maxit)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    vox_its = float(sum(sp["n"] ** 3 * int(its[i].sum()) for i, sp in enumerate(specs)))
+    t0 = time.perf_counter()
+    seq_its = 0.0
+    max_rel = 0.0
+    for i, (sp, g) in enumerate(zip(specs, grids)):
+        Cs, it_s, rcs = g.effective_stiffness(sch, 1e-8, args.batch_maxit)
+        seq_its += sp["n"] ** 3 * float(np.sum(it_s))
+        max_rel = max(max_rel, float(np.abs(C[i] - Cs).max() / np.abs(Cs).max()))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    return {"experiment": "batch", "cells": len(specs), "loads": 6 * len(specs), "status": gfp.STATUS[rc],
+            "sizes": {str(n): sum(1 for sp in specs if sp["n"] == n) for n in sorted(tuned)},
+            "tiles": {str(k): v for k, v in tuned.items()},
+            "batch": {"seconds": t_batch, "voxel_iterations": vox_its, "voxel-iterations/s": vox_its / t_batch},
+            "sequential": {"seconds": t_seq, "voxel_iterations": seq_its, "voxel-iterations/s": seq_its / t_seq},
+            "speedup": t_seq / t_batch, "C_eff_max_rel_diff_batch_vs_sequential": max_rel,
+            "inner_iterations": {"min": int(its.min()), "max": int(its.max()), "total": int(its.sum())}}
+
+
 def oracle_sample(n, op, iters):
     """Time the FP64 oracle as it stands on `iters` iterations of the same workload."""
     from oracle import gfp_oracle as O
@@ -338,9 +384,11 @@ def main():
     ap.add_argument("--ttt-maxit", type=int, default=3000)
     ap.add_argument("--tune", type=int, default=1, help="run the tile autotuner before timing")
     ap.add_argument("--tiles", default="", help="x lines,y columns,z columns (negative z: TMA z-pass)")
-    ap.add_argument("--experiment", default="", help="conv3d: iterations vs contrast for the paper's 3D cell")
+    ap.add_argument("--experiment", default="", help="conv3d: iterations vs contrast for the paper's 3D cell; batch: batched homogenization")
     ap.add_argument("--conv-tol", type=float, default=1e-8)
     ap.add_argument("--conv-maxit-f", type=int, default=3000)
+    ap.add_argument("--batch-count", type=int, default=32)
+    ap.add_argument("--batch-maxit", type=int, default=20000)
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--passes-only", type=int, default=0,
@@ -371,6 +419,9 @@ def main():
         return
     if args.experiment == "conv3d":
         convergence_experiment(args)
+        return
+    if args.experiment == "batch":
+        print(json.dumps(batch_experiment(args)))
         return
     rank, world, local = dist_setup()
     line = run_gfp(args, rank, world, local)

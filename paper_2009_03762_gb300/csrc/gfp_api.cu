@@ -47,6 +47,7 @@ __global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, S
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    st->restart = 0;  // the x-pass of this iteration has run
     const double* t = st->T0;
     const double t0 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + 2.0 * (t[3] * t[3] + t[4] * t[4] + t[5] * t[5]);
     const double sum = sh[0];
@@ -130,7 +131,11 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
 }
 
 // Mean of the six FP32 correction components, accumulated in FP64 (stage 1: per-block partials).
-__global__ void corr_mean_partial_kernel(const float* __restrict__ corr, long long N, double* __restrict__ part) {
+// gate (may be null): skip while the inner state is paused at its window cap (state 2), i.e. unless
+// an FP64 outer pass follows
+__global__ void corr_mean_partial_kernel(const float* __restrict__ corr, long long N, double* __restrict__ part,
+                                         const SolveState* gate) {
+  if (gate && gate->done == 2) return;
   __shared__ double sh[6][256];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
@@ -149,7 +154,9 @@ __global__ void corr_mean_partial_kernel(const float* __restrict__ corr, long lo
 }
 
 // stage 2: one block, fixed order
-__global__ void corr_mean_final_kernel(const double* __restrict__ part, int nb, long long N, double* __restrict__ mean) {
+__global__ void corr_mean_final_kernel(const double* __restrict__ part, int nb, long long N, double* __restrict__ mean,
+                                       const SolveState* gate) {
+  if (gate && gate->done == 2) return;
   if (threadIdx.x < 6) {
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += part[b * 6 + threadIdx.x];
@@ -289,12 +296,29 @@ struct BatchAcc {
   int outer;  // FP64 outer passes
 };
 
-// Start the inner window of one (microstructure, load) slot after its FP64 residual pass: count the
-// previous window's iterations, then re-arm the inner state with the target max(tol/2, ratio eta_64)
-// and the reference stress norm of the outer pass; a converged slot leaves its inner state done.
-__global__ void batch_arm_kernel(const SolveState* __restrict__ st, SolveState* __restrict__ st_in, BatchAcc* acc,
+// Start of a slot's window: if its inner iterations stopped at the window cap (state 2) they continue
+// for another window and the FP64 outer pass is held (DONE_HELD makes its kernels no-ops); otherwise
+// (first window, inner target reached, inner divergence) the outer pass runs.
+__global__ void batch_gate_kernel(SolveState* __restrict__ st, SolveState* __restrict__ st_in, int window) {
+  if (threadIdx.x != 0 || st->done) return;
+  if (st_in->done == 2) {
+    st->done = DONE_HELD;
+    st_in->done = 0;
+    st_in->maxit += window;
+  }
+}
+
+// After the (possibly held) FP64 residual pass: a held slot resumes its inner iterations; otherwise
+// count the finished inner solve's iterations and re-arm the inner state from a zero correction with
+// the target max(tol/2, ratio eta_64) and the reference stress norm of the outer pass; a converged
+// slot leaves its inner state done.
+__global__ void batch_arm_kernel(SolveState* __restrict__ st, SolveState* __restrict__ st_in, BatchAcc* acc,
                                  double tol, double ratio, int window) {
   if (threadIdx.x != 0) return;
+  if (st->done == DONE_HELD) {
+    st->done = 0;
+    return;
+  }
   acc->inner += st_in->it;
   st_in->it = 0;
   if (st->done) {
@@ -308,6 +332,7 @@ __global__ void batch_arm_kernel(const SolveState* __restrict__ st, SolveState* 
   st_in->eta = INFINITY;
   st_in->eta_min = INFINITY;
   st_in->tol = fmax(0.5 * tol, ratio * st->eta);
+  st_in->restart = 1;
   for (int c = 0; c < 6; ++c) st_in->T0[c] = st->T0[c];
 }
 
@@ -797,8 +822,8 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     inner_total += g->st_in_host->it;
     if (g->st_in_host->done == 3) { status = GFP_ERR_DIVERGED; break; }
     if (g->st_in_host->done == DONE_TIMEOUT) { status = GFP_ERR_DEVICE_TIMEOUT; break; }
-    corr_mean_partial_kernel<<<cvb, 256, 0, g->stream>>>(g->eps32, d.N, g->cpart);
-    corr_mean_final_kernel<<<1, 32, 0, g->stream>>>(g->cpart, cvb, d.N, g->cmean);
+    corr_mean_partial_kernel<<<cvb, 256, 0, g->stream>>>(g->eps32, d.N, g->cpart, nullptr);
+    corr_mean_final_kernel<<<1, 32, 0, g->stream>>>(g->cpart, cvb, d.N, g->cmean, nullptr);
     // the next outer pass re-arms the FP64 state (it counts outer passes; never stops on maxit)
     g->st_host->done = 0;
     GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
@@ -1685,6 +1710,7 @@ void slot_window(BatchSlot& s, const GammaParams<double>& gp64, const GammaParam
   const Dims& d = g->d;
   cudaStream_t st = s.stream;
   const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+  batch_gate_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, window);
   Passes<double>::pass_x(st, s.lc64, s.spec, s.eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0, s.eps32, s.cmean,
                          s.st);
   Passes<double>::pass_y(st, s.lc64, false, s.spec, g->tw64[1], g->plan[1], d, s.st);
@@ -1693,15 +1719,15 @@ void slot_window(BatchSlot& s, const GammaParams<double>& gp64, const GammaParam
   batch_arm_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, s.acc, tol, kInnerReduction, window);
   float2* spec32 = reinterpret_cast<float2*>(s.spec);
   for (int k = 0; k < window; ++k) {
-    Passes<float>::pass_x(st, s.lc32, spec32, s.eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d,
-                          k == 0 ? PX_ZERO : PX_DELTA, nullptr, nullptr, s.st_in);
+    Passes<float>::pass_x(st, s.lc32, spec32, s.eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, PX_DELTA,
+                          nullptr, nullptr, s.st_in);
     Passes<float>::pass_y(st, s.lc32, false, spec32, g->tw32[1], g->plan[1], d, s.st_in);
     Passes<float>::pass_z(st, s.lc32, spec32, g->tw32[2], g->plan[2], d, gp32, s.partials, s.st_in, PZ_INNER, s.vsrc);
     launch_reduce_eta(st, s.partials, s.lc32.z_blocks, s.st_in, nullptr, 0);
     Passes<float>::pass_y(st, s.lc32, true, spec32, g->tw32[1], g->plan[1], d, s.st_in);
   }
-  corr_mean_partial_kernel<<<cvb, 256, 0, st>>>(s.eps32, d.N, s.cpart);
-  corr_mean_final_kernel<<<1, 32, 0, st>>>(s.cpart, cvb, d.N, s.cmean);
+  corr_mean_partial_kernel<<<cvb, 256, 0, st>>>(s.eps32, d.N, s.cpart, s.st_in);
+  corr_mean_final_kernel<<<1, 32, 0, st>>>(s.cpart, cvb, d.N, s.cmean, s.st_in);
 }
 
 }  // namespace

@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(512) pass_y_c_kernel(typename C<R>::T* __restr
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   const int cols = COLS > 0 ? COLS : cols_arg;
-  if (st->done) return;
+  // the inverse pass runs after the residual reduction of its iteration: it still completes an
+  // iteration stopped by the iteration cap (state 2), so that a batched solve resumes from a fully
+  // transformed increment
+  if (st->done && !(INV && st->done == 2)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + N;
@@ -482,8 +485,8 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
   const int p = fl / lines, l = fl % lines;
   const long long li = line0 + l;
   const bool live = (fl < 3 * lines) && (li < nlines);
-  const bool have_delta = (flags & PX_DELTA) != 0;
-  const bool zero = (flags & PX_ZERO) != 0;
+  const bool zero = (flags & PX_ZERO) != 0 || st->restart;
+  const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
   const SLine<T, true> sl{buf + fl * LP, 1};
   T v[P::E];
   if (have_delta) {
@@ -655,8 +658,8 @@ __global__ void __launch_bounds__(512) pass_x_a_kernel(typename C<R>::T* __restr
   R* sst = reinterpret_cast<R*>(buf + 3 * lines * LP);       // [8][lines][N]: eps 0..5, lambda, mu
   const long long nlines = (long long)d.n2 * d.n3;
   const long long line0 = (long long)blockIdx.x * lines;
-  const bool have_delta = (flags & PX_DELTA) != 0;
-  const bool zero = (flags & PX_ZERO) != 0;
+  const bool zero = (flags & PX_ZERO) != 0 || st->restart;
+  const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
   // ---- stage everything this CTA reads
   {
     constexpr int spec_chunks = SP * (int)sizeof(T) / 16;     // 16-byte granules per spectrum row

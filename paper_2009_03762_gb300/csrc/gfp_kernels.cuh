@@ -33,8 +33,9 @@ struct Dims {
 };
 
 // SolveState::done values besides 0 (running): 1 converged, 2 maxit, 3 diverged, DONE_TIMEOUT when a
-// bounded device-side wait gave up.
-enum { DONE_TIMEOUT = 4 };
+// bounded device-side wait gave up; DONE_HELD (batched solves only) holds a slot's FP64 outer pass
+// for one window while its inner iterations continue.
+enum { DONE_TIMEOUT = 4, DONE_HELD = 5 };
 
 // Device-side solver state; one per solve, reset by the host before the first iteration.
 struct SolveState {
@@ -42,6 +43,7 @@ struct SolveState {
   int done;        // 0 running, 1 converged, 2 maxit reached, 3 diverged
   int maxit;
   int growth;      // consecutive iterations with growing eta
+  int restart;     // 1: the next x-pass starts from a zero strain correction (PX_ZERO); reduce_eta clears it
   double tol;
   double eta;      // last residual
   double eta_min;
@@ -230,8 +232,8 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
   const int n1 = d.n1, n1h = d.n1h;
   const long long nlines = (long long)d.n2 * d.n3;
   const long long line0 = (long long)blockIdx.x * lines;
-  const bool have_delta = (flags & PX_DELTA) != 0;
-  const bool zero = (flags & PX_ZERO) != 0;
+  const bool zero = (flags & PX_ZERO) != 0 || st->restart;
+  const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
   for (int i = threadIdx.x; i < n1; i += blockDim.x) twl[i] = tw[i];
   const int tot_lines = 3 * lines;
   if (have_delta) {
@@ -343,7 +345,7 @@ template <typename R, bool INV>
 __global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typename C<R>::T* __restrict__ tw,
                               FftPlan plan, Dims d, int cols, const SolveState* __restrict__ st) {
   typedef typename C<R>::T T;
-  if (st->done) return;
+  if (st->done && !(INV && st->done == 2)) return;  // as in pass_y_c_kernel
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* twl = reinterpret_cast<T*>(smem_raw);
   T* buf = twl + d.n2;                       // [n2][cols], plus a ping-pong copy
