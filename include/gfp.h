@@ -121,9 +121,11 @@ int gfp_grad(gfp_grid g, const gfp_scheme* scheme, int I, int J, double tol, int
 /* Batched homogenization (no counterpart in the paper): the six Voigt load cases of `count` cells of
  * possibly different sizes, mixed precision only (FP32 inner iterations, FP64 residual, mean strain and
  * refinement; schemes CD, ACD, AHC, AFB_R).  Every (cell, load) pair is a slot with its own device
- * state; one CUDA graph holds a window of every slot (one FP64 residual pass and 32 FP32 iterations) as
- * parallel branches, and the graph is replayed until all slots reach eta < tol or maxit iterations.
- * Converged slots turn into no-ops on the device.  C_eff_out: count x 36 (row-major Voigt per cell);
+ * state; one CUDA graph holds a window of every running slot (32 FP32 iterations, preceded by an FP64
+ * residual pass when the slot's inner solve has reached its target) as parallel branches, and the graph
+ * is replayed until all slots reach eta < tol or maxit iterations.  Finished slots turn into no-ops on
+ * the device, and the graph is captured again without them whenever the running slots have halved.
+ * The iterates and results equal those of gfp_effective_stiffness.  C_eff_out: count x 36 (row-major Voigt per cell);
  * iters_out (may be NULL): count x 6 inner iterations per load.  The cells must have their phases set.
  * Slot buffers (about 230 bytes per voxel per load) are allocated for the call and freed at its end. */
 int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* scheme, double tol, int maxit, double* C_eff_out,

@@ -336,15 +336,19 @@ __global__ void batch_arm_kernel(SolveState* __restrict__ st, SolveState* __rest
   for (int c = 0; c < 6; ++c) st_in->T0[c] = st->T0[c];
 }
 
-// 1 if every slot's outer state is done (converged, diverged or timed out).
-__global__ void batch_all_done_kernel(SolveState* const* __restrict__ sts, int n, int* flag) {
-  __shared__ int any_running;
-  if (threadIdx.x == 0) any_running = 0;
+// After a window: running[i] = 1 while slot i's outer state is still running, and the number of
+// running slots.
+__global__ void batch_status_kernel(SolveState* const* __restrict__ sts, int n, int* running, int* count) {
+  __shared__ int c;
+  if (threadIdx.x == 0) c = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (sts[i]->done == 0) any_running = 1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = sts[i]->done == 0;
+    running[i] = r;
+    if (r) atomicAdd(&c, 1);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) *flag = any_running ? 0 : 1;
+  if (threadIdx.x == 0) *count = c;
 }
 
 }  // namespace gfp
@@ -1788,12 +1792,14 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
       s.lc32.ztmap = encode_ztmap(&s.zm32, s.spec, d, s.lc32.z_cols, 4) ? &s.zm32 : nullptr;
       st_ptrs[i * 6 + J] = s.st;
     }
-  int* d_flag = nullptr;
+  int* d_count = nullptr;
+  int* d_running = nullptr;
   SolveState** d_sts = nullptr;
   cudaStream_t main = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc(&d_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_running, sizeof(int) * nslots);
   if (e == cudaSuccess) e = cudaMalloc(&d_sts, sizeof(SolveState*) * nslots);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
   if (e == cudaSuccess)
@@ -1820,42 +1826,57 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
     }
     e = cudaDeviceSynchronize();
   }
-  // capture one window of every slot as parallel branches of one graph
-  if (e == cudaSuccess) {
-    cudaEvent_t fork;
-    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    std::vector<cudaEvent_t> joins(nslots, nullptr);
-    for (int i = 0; i < nslots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+  // one window of every running slot as parallel branches of one graph; the graph is captured again
+  // without the finished slots whenever the running ones have halved (finished slots would otherwise
+  // keep costing a launch per kernel and window)
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(nslots, nullptr);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int i = 0; i < nslots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+  auto capture = [&](const std::vector<int>& active) {
+    if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+    if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaEventRecord(fork, main);
-      for (int i = 0; i < nslots; ++i) {
-        BatchSlot& s = slots[i];
-        cudaStreamWaitEvent(s.stream, fork, 0);
-        const GammaParams<double> gp64 = gamma_params<double>(s.g, sc->op, s.g->tabA, s.g->tabB);
-        const GammaParams<float> gp32 = gamma_params<float>(s.g, sc->op, s.g->tabA32, s.g->tabB32);
-        slot_window(s, gp64, gp32, tol, window);
-        cudaEventRecord(joins[i], s.stream);
-        cudaStreamWaitEvent(main, joins[i], 0);
-      }
-      batch_all_done_kernel<<<1, 256, 0, main>>>(d_sts, nslots, d_flag);
-      e = cudaStreamEndCapture(main, &graph);
+    if (e != cudaSuccess) return;
+    cudaEventRecord(fork, main);
+    for (int i : active) {
+      BatchSlot& s = slots[i];
+      cudaStreamWaitEvent(s.stream, fork, 0);
+      const GammaParams<double> gp64 = gamma_params<double>(s.g, sc->op, s.g->tabA, s.g->tabB);
+      const GammaParams<float> gp32 = gamma_params<float>(s.g, sc->op, s.g->tabA32, s.g->tabB32);
+      slot_window(s, gp64, gp32, tol, window);
+      cudaEventRecord(joins[i], s.stream);
+      cudaStreamWaitEvent(main, joins[i], 0);
     }
+    batch_status_kernel<<<1, 256, 0, main>>>(d_sts, nslots, d_running, d_count);
+    e = cudaStreamEndCapture(main, &graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaEventDestroy(fork);
-    for (auto ev : joins) if (ev) cudaEventDestroy(ev);
-  }
+  };
+  std::vector<int> active(nslots);
+  for (int i = 0; i < nslots; ++i) active[i] = i;
+  capture(active);
   // replay until every slot has converged (or the iteration budget is spent)
   int windows = 0;
   const int max_windows = std::max(1, (maxit + window - 1) / window);
+  std::vector<int> running(nslots);
   while (e == cudaSuccess && windows < max_windows) {
     e = cudaGraphLaunch(exec, main);
     ++windows;
-    int flag = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, main);
+    int count = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, main);
     if (e == cudaSuccess) e = cudaStreamSynchronize(main);
-    if (flag) break;
+    if (e != cudaSuccess || count == 0) break;
+    if (2 * count <= (int)active.size()) {
+      e = cudaMemcpy(running.data(), d_running, sizeof(int) * nslots, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      active.clear();
+      for (int i = 0; i < nslots; ++i)
+        if (running[i]) active.push_back(i);
+      capture(active);
+    }
   }
+  if (fork) cudaEventDestroy(fork);
+  for (auto ev : joins) if (ev) cudaEventDestroy(ev);
   // slots still running after the budget: the last outer pass holds their best FP64 state
   if (e == cudaSuccess) {
     int all_done = 1;
@@ -1890,7 +1911,8 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (main) cudaStreamDestroy(main);
-  cudaFree(d_flag);
+  cudaFree(d_count);
+  cudaFree(d_running);
   cudaFree(d_sts);
   for (auto& s : slots) free_slot(s);
   return rc;
