@@ -78,8 +78,19 @@ struct SLine {
   __device__ __forceinline__ T& operator[](int e) const { return base[(PAD ? e + (e >> 4) : e) * es]; }
 };
 
-template <int N, int S, bool INV, typename T, bool PAD>
-__device__ __forceinline__ void cexchange(T* v, SLine<T, PAD> sm, int t) {
+// Line L of the 8-column z tile (rows of 48 elements: component c, column cc at 8 c + cc) with the
+// columns of odd rows XOR-swizzled by 8, i.e. one component further: the Green step's half-warps
+// (2 rows x 8 columns of one component) then touch every bank once, while the line transforms'
+// access patterns keep their bank spread.
+template <typename T>
+struct SLineX {
+  T* base;
+  int L;
+  __device__ __forceinline__ T& operator[](int e) const { return base[e * 48 + (L ^ ((e & 1) << 3))]; }
+};
+
+template <int N, int S, bool INV, typename T, typename SL>
+__device__ __forceinline__ void cexchange(T* v, SL sm, int t) {
   typedef CPlan<N> P;
   constexpr int R = P::R(S), R1 = P::R(S + 1);
 #pragma unroll
@@ -97,8 +108,8 @@ __device__ __forceinline__ void cexchange(T* v, SLine<T, PAD> sm, int t) {
 // Full transform of one line held as v[b R0 + r] = x[cin_idx<N,0>(t,b,r)]; on return
 // v[b RL + r] = X[cout_idx<N,NST-1>(t,b,r)] = X[t + b T + r N / RL].  Every thread of the block
 // must call it (it synchronises).
-template <int N, bool INV, typename T, bool PAD>
-__device__ __forceinline__ void cfft(T* v, SLine<T, PAD> sm, int t, const T* __restrict__ tw) {
+template <int N, bool INV, typename T, typename SL>
+__device__ __forceinline__ void cfft(T* v, SL sm, int t, const T* __restrict__ tw) {
   typedef CPlan<N> P;
   cstage<N, 0, INV>(v, t, tw);
   if constexpr (P::NST > 1) {
@@ -166,12 +177,13 @@ template <typename R, int N> struct ZBound {
 };
 
 // Green step on a z-tile in shared memory: rows [k3][ZS] holding 6 components x cols columns
-// (component c, column cc at c cols + cc).  Residual partial of the thread (returned), T(0), and, by
-// mode, the increment written back in place (PZ_GAMMA, PZ_INNER, PZ_DGO) or the inner-iteration
-// source stored (PZ_RESIDUAL).  vs: the tile's inner source staged as [3][N][cols], or null to read
-// it from global memory.  blockDim.x is a multiple of cols: every thread keeps one column.
+// (component c, column cc at c cols + cc, XOR swz on odd rows).  Residual partial of the thread
+// (returned), T(0), and, by mode, the increment written back in place (PZ_GAMMA, PZ_INNER, PZ_DGO) or
+// the inner-iteration source stored (PZ_RESIDUAL).  vs: the tile's inner source staged as
+// [3][N][cols], or null to read it from global memory.  blockDim.x is a multiple of cols: every
+// thread keeps one column.
 template <typename R, int N>
-__device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int ZS, int cols,
+__device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int ZS, int cols, int swz,
                                         const typename C<R>::T* __restrict__ ab3, const float2* vs, const Dims& d,
                                         int k10, int k2, const GammaParams<R>& gp, SolveState* __restrict__ st,
                                         int mode, float2* __restrict__ vsrc) {
@@ -186,11 +198,29 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
     const bool ny1 = ((d.n1 & 1) == 0) && (2 * k1 == d.n1);
     const bool self1 = (k1 == 0) || ny1;
     const int zstep = blockDim.x / cols;
-    for (int z = threadIdx.x / cols; z < N; z += zstep) {
-      T* row = buf + z * ZS + cc;
+    // inner source of point z: staged tile or global memory
+    auto source = [&](int z, float2& s1, float2& s2, float2& s3) {
+      if (vs) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
+      else {
+        const long long vi = d.row(z, k2) * d.P + k1;
+        s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi];
+      }
+    };
+    // the next point's source is loaded one point ahead, so its latency overlaps this point's arithmetic
+    float2 p1, p2, p3;
+    const int z0 = threadIdx.x / cols;
+    if (mode == PZ_INNER && z0 < N) source(z0, p1, p2, p3);
+    for (int z = z0; z < N; z += zstep) {
+      float2 s1, s2, s3;
+      if (mode == PZ_INNER) {
+        s1 = p1; s2 = p2; s3 = p3;
+        if (z + zstep < N) source(z + zstep, p1, p2, p3);
+      }
+      T* rowz = buf + z * ZS;
+      const int sw = (z & 1) ? swz : 0;
       T tt[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) tt[c] = row[c * cols];
+      for (int c = 0; c < 6; ++c) tt[c] = rowz[(c * cols + cc) ^ sw];
       const T ab = ab3[z];
       const R a3 = ab.x, b3 = ab.y;
       const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
@@ -203,9 +233,6 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
       T v1, v2, v3;
       tk_vec<R>(tt, kt1, kt2, kt3, v1, v2, v3);
       if (mode == PZ_INNER) {
-        float2 s1, s2, s3;
-        if (vs) { s1 = vs[z * cols + cc]; s2 = vs[(N + z) * cols + cc]; s3 = vs[(2 * N + z) * cols + cc]; }
-        else { s1 = vsrc[vi]; s2 = vsrc[d.S + vi]; s3 = vsrc[2 * d.S + vi]; }
         v1.x += (R)s1.x; v1.y += (R)s1.y; v2.x += (R)s2.x; v2.y += (R)s2.y; v3.x += (R)s3.x; v3.y += (R)s3.y;
       }
       R r2 = vnorm2(v1, v2, v3);
@@ -225,7 +252,7 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
       if (mode == PZ_DGO) {
         dgo_apply_point<R>(tt, gp.dgo, vi, d.S, gp.invN, o);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
+        for (int c = 0; c < 6; ++c) rowz[(c * cols + cc) ^ sw] = o[c];
         continue;
       }
       gamma0_from_v<R>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
@@ -236,7 +263,7 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
         for (int c = 0; c < 6; ++c) { o[c].x = (R)0.5 * (o[c].x + o2[c].x); o[c].y = (R)0.5 * (o[c].y + o2[c].y); }
       }
 #pragma unroll
-      for (int c = 0; c < 6; ++c) row[c * cols] = o[c];
+      for (int c = 0; c < 6; ++c) rowz[(c * cols + cc) ^ sw] = o[c];
     }
   }
   return acc;
@@ -311,7 +338,7 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   if (stage_v) cp_async_wait_all();
   __syncthreads();
   // Green operator, residual and T(0) per (k3, column)
-  const R acc = green_tile<R, N>(buf, ZS, cols, ab3, stage_v ? vs : nullptr, d, k10, k2, gp, st, mode, vsrc);
+  const R acc = green_tile<R, N>(buf, ZS, cols, 0, ab3, stage_v ? vs : nullptr, d, k10, k2, gp, st, mode, vsrc);
   double accd = (double)acc;
   for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
@@ -367,7 +394,8 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_c2_kernel(typename
     const int gr = i % (COLS / 2), rz = i / (COLS / 2);
     const int z = rz % N, c = 3 + rz / N;
     if (k10 + 2 * gr >= d.P) continue;
-    cp_async16(buf + z * ZS + c * COLS + 2 * gr, spec + c * d.S + d.row(z, k2) * d.P + k10 + 2 * gr);
+    const int sw = (z & 1) ? 8 : 0;
+    cp_async16(buf + z * ZS + ((c * COLS + 2 * gr) ^ sw), spec + c * d.S + d.row(z, k2) * d.P + k10 + 2 * gr);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -383,7 +411,7 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_c2_kernel(typename
   const int zs = (int)d.zstride();  // N zs < 2^31 for every supported grid
   T* gA = spec + (l / COLS) * d.S + d.row(0, k2) * d.P + k10 + col;
   T* gB = gA + 3 * d.S;
-  const SLine<T, false> slA{buf + l, ZS}, slB{buf + l + 24, ZS};
+  const SLineX<T> slA{buf, l}, slB{buf, l + 24};
   constexpr int RL = P::R(P::NST - 1);
   T v[P::E];
   // line A: global -> registers -> forward transform -> tile
@@ -419,7 +447,7 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_c2_kernel(typename
 #pragma unroll
     for (int r = 0; r < RL; ++r) slB[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
   __syncthreads();
-  const R acc = green_tile<R, N>(buf, ZS, COLS, ab3, nullptr, d, k10, k2, gp, st, mode, vsrc);
+  const R acc = green_tile<R, N>(buf, ZS, COLS, 8, ab3, nullptr, d, k10, k2, gp, st, mode, vsrc);
   double accd = (double)acc;
   for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
