@@ -1,0 +1,73 @@
+"""Full-size checks (256^3, the benchmark's grid) in the benchmark's launch configuration: mixed
+precision with x-pass tiles of 2 lines, y tiles of 16 columns and the 8-column two-line z-pass.
+The dense-DFT oracle cannot run at this size, so the checks use properties that hold at any size:
+the closed-form response of a laminate, and agreement with the FP64 GPU solve."""
+import numpy as np
+import pytest
+
+from paper_2009_03762_gb300 import microstructure as M
+
+pytestmark = pytest.mark.gpu
+
+BENCH_TILES = [2, 16, 8]
+
+
+@pytest.fixture(scope="module")
+def gfp():
+    from paper_2009_03762_gb300 import gfp as G
+    G.lib()
+    return G
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+def test_laminate_256_along_x3_closed_form(gfp):
+    """Layers stacked along x3 (the z-pass couples them): the normal stress s33 and the shears s13,
+    s23 are uniform, so s33 = (E33 + <l/M>(E11 + E22)) / <1/M>, M = l + 2 mu, and
+    s13 = E13 / <1/(2 mu)> (tensor components, no factor 2)."""
+    n = 256
+    rng = np.random.Generator(np.random.PCG64(21))
+    Ey = np.exp(rng.uniform(np.log(0.5), np.log(20.0), size=n))
+    nu = rng.uniform(0.15, 0.4, size=n)
+    l3, m3 = M.lame(Ey, nu)
+    lam = np.broadcast_to(l3[:, None, None], (n, n, n)).copy()
+    mu = np.broadcast_to(m3[:, None, None], (n, n, n)).copy()
+    E = np.array([0.004, -0.002, 0.01, 0.003, -0.002, 0.001])
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu)
+    g.set_tiles(gfp.MIXED, BENCH_TILES)
+    r = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), E, 1e-10, 20000)
+    assert r.converged
+    Mm = l3 + 2 * m3
+    s33 = (E[2] + np.mean(l3 / Mm) * (E[0] + E[1])) / np.mean(1 / Mm)
+    s13 = E[4] / np.mean(1 / (2 * m3))
+    s23 = E[3] / np.mean(1 / (2 * m3))
+    np.testing.assert_allclose([r.sigma_mean[2], r.sigma_mean[4], r.sigma_mean[3]], [s33, s13, s23], rtol=1e-7)
+    eps = g.strain()
+    # in-plane strains stay uniform and equal to the prescribed mean
+    for c in (0, 1, 5):
+        np.testing.assert_allclose(eps[c], E[c], atol=1e-8)
+    g.close()
+
+
+def test_bench_cell_256_mixed_matches_fp64(gfp):
+    """The benchmark's random-sphere cell solved to eta < 1e-8 in mixed precision (bench tiles) and in
+    FP64: mean stress within 1e-6 and strain field within 1e-5 relative; the FP64 mean strain is held."""
+    n = 256
+    lam, mu = M.random_spheres(n, vf=0.25, rmin=6.0, rmax=16.0, contrast=100.0, seed=0)
+    E = [0.0, 0.0, 0.0, 0.0, 0.0, 1.0]
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu)
+    g.set_tiles(gfp.MIXED, BENCH_TILES)
+    rm = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), E, 1e-8, 20000)
+    assert rm.converged and rm.residual < 1e-8
+    eps_m = g.strain()
+    np.testing.assert_allclose(eps_m.reshape(6, -1).mean(axis=1), E, atol=1e-12)
+    r64 = g.solve(gfp.scheme("AFB_R", "PCD", "FP64"), E, 1e-8, 20000)
+    assert r64.converged
+    eps_64 = g.strain()
+    assert _rel(rm.sigma_mean, r64.sigma_mean) <= 1e-6
+    assert _rel(eps_m, eps_64) <= 1e-5
+    g.close()
