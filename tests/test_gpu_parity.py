@@ -103,6 +103,22 @@ def test_laminate_closed_form_on_gpu(gfp, op):
     np.testing.assert_allclose([r.sigma_mean[0], r.sigma_mean[5]], [s11, s12], rtol=1e-9)
 
 
+@pytest.mark.parametrize("op", ["F", "HC", "AFB_R"])
+def test_1d_matrix_inclusion_matches_paper_closed_form(gfp, op):
+    """1D matrix-inclusion example of Sec. 4 on n x 1 x 1 grids (n = 18, 54, 162): the nodal strain of
+    the closed form of Sec. 2.1 (tests/golden/mi1d_sharp.txt), C_I/C_M = 100 as lambda = 0, mu = C/2."""
+    rows = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mi1d_sharp.txt"))
+    for n in (18, 54, 162):
+        sel = rows[rows[:, 0] == n]
+        nu, E_ref = sel[:, 2], sel[:, 3]
+        C = 1.0 + 99.0 * nu
+        lam = np.zeros((1, 1, n))
+        mu = (0.5 * C).reshape(1, 1, n)
+        r, eps = gfp.solve(lam, mu, op, [1.0, 0, 0, 0, 0, 0], tol=1e-11, maxit=5000)
+        assert r.converged
+        np.testing.assert_allclose(eps[0, 0, 0], E_ref, rtol=1e-9)
+
+
 def test_full_size_iterations_match_oracle_128(gfp):
     """128^3 smooth cube (config size): three iterations element by element against the oracle."""
     lam, mu = M.smooth_cube(128, 64, 10.0, width=2.0)
