@@ -23,7 +23,7 @@ modeling of the quasi-static mechanical behavior of inhomogeneous materials"):
   operator Gamma^c built from the alias sum as printed (Sec. 5.4, Algorithm D-3D, with
   the isotropic G_H and Gamma_H of the same section).
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
 * stopping rule: the default is the equilibrium residual
   eta = ||T(k) q^b(k)||_2 / ||T(k=0)||_F over all modes (unitary DFT, so this equals
   ||div^b T|| / (sqrt(N) ||mean T||)); the paper's own rule (L1 norm of the difference of
@@ -351,12 +351,16 @@ class Result:
 
 def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=None,
           stop_rule=0, dgo_m=None, dgo_table=None, max_iters_exact=None, dgo_form="polarization",
-          dgo_power=2):
+          dgo_power=2, estar=None):
     """Solve the periodic cell problem with Algorithm T-3D (disc='TD'), P-3D (disc='PCD') or D-3D (DGO).
 
     lam, mu: (n3, n2, n1) voxel Lame fields (already sampled at x_i or x_i^c).
     E_macro: 6 tensor components (11,22,33,23,13,12) of the prescribed mean strain.
     max_iters_exact: if set, run exactly that many iterations regardless of tol.
+    estar: optional eigenstrain field, (6, n3, n2, n1) tensor components in the same order.  The
+    stress-strain relation becomes T = C[E - E_*] and the initial stress of the algorithm
+    T^(0) = C_i [E_bar - E_*i] (the generalization stated at the end of Sec. 6); the iteration is
+    otherwise unchanged.  Not defined here for Algorithm D.
     """
     lam = np.asarray(lam, np.float64)
     mu = np.asarray(mu, np.float64)
@@ -365,8 +369,13 @@ def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=
     lam_h, mu_h = default_reference(lam, mu) if ref is None else ref
     Ebar = voigt_to_tensor(np.asarray(E_macro, np.float64))
     Ebar_f = Ebar[:, :, None, None, None] * np.ones((1, 1, n3, n2, n1))
-    T0 = stiffness_apply(lam, mu, Ebar_f)
+    if estar is None:
+        T0 = stiffness_apply(lam, mu, Ebar_f)
+    else:
+        T0 = stiffness_apply(lam, mu, Ebar_f - voigt_to_tensor(np.asarray(estar, np.float64)))
     if scheme == "DGO":
+        if estar is not None:
+            raise ValueError("eigenstrain is not defined for Algorithm D here")
         return _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_table, max_iters_exact,
                           dgo_form, dgo_power)
     mats = [dft_matrices(nr, h, disc) for nr in (n1, n2, n3)]

@@ -260,6 +260,58 @@ def test_laminate_exact_effective_response(scheme, n1):
     np.testing.assert_allclose(r.eps[0], np.broadcast_to(e11, r.eps[0].shape), rtol=1e-8, atol=1e-12)
 
 
+def _laminate_eigenstrain_closed_form(lam1, mu1, es, E):
+    """Exact response of a laminate along x1 with a layer-wise eigenstrain es (6, n1), stress
+    T = C[E - E_*] (generalization at the end of Sec. 6).  The tractions on the layer planes,
+    sigma_11, sigma_12, sigma_13, are uniform; eps_22, eps_33, eps_23 equal their means.
+    Returns the 6 mean stresses and the fields eps_11, eps_12 across the layers."""
+    E11, E22, E33, E23, E13, E12 = E
+    M_ = lam1 + 2 * mu1
+    tr_s = es[0] + es[1] + es[2]
+    a = lam1 * (E22 + E33 - tr_s) - 2 * mu1 * es[0]          # sigma_11 = M eps_11 + a
+    s11 = (E11 + np.mean(a / M_)) / np.mean(1.0 / M_)
+    e11 = (s11 - a) / M_
+    s12 = (E12 - np.mean(es[5])) / np.mean(1.0 / (2 * mu1))   # sigma_12 = 2 mu (eps_12 - es_12)
+    s13 = (E13 - np.mean(es[4])) / np.mean(1.0 / (2 * mu1))
+    e12 = s12 / (2 * mu1) + es[5]
+    tr = e11 + E22 + E33 - tr_s
+    s22 = np.mean(lam1 * tr + 2 * mu1 * (E22 - es[1]))
+    s33 = np.mean(lam1 * tr + 2 * mu1 * (E33 - es[2]))
+    s23 = np.mean(2 * mu1 * (E23 - es[3]))
+    return np.array([s11, s22, s33, s23, s13, s12]), e11, e12
+
+
+@pytest.mark.parametrize("scheme", ["F", "HC", "AFB_R"])
+def test_laminate_with_eigenstrain_closed_form(scheme):
+    """Eigenstrain generalization (Sec. 6): a laminate with layer-wise moduli and eigenstrain."""
+    n1 = 8
+    lam, mu = M.random_laminate(n1, 3, 4, seed=7)
+    rng = np.random.Generator(np.random.PCG64(11))
+    es1 = rng.uniform(-0.01, 0.01, size=(6, n1))
+    es = np.broadcast_to(es1[:, None, None, :], (6, 4, 3, n1)).copy()
+    E = np.array([0.004, -0.002, 0.003, 0.001, -0.002, 0.005])
+    r = O.solve(lam, mu, scheme, E, tol=1e-12, maxit=3000, estar=es)
+    assert r.converged
+    ref, e11, e12 = _laminate_eigenstrain_closed_form(lam[0, 0], mu[0, 0], es1, E)
+    np.testing.assert_allclose(r.sigma_mean, ref, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(r.eps[0], np.broadcast_to(e11, r.eps[0].shape), rtol=1e-8, atol=1e-13)
+    np.testing.assert_allclose(r.eps[5], np.broadcast_to(e12, r.eps[5].shape), rtol=1e-8, atol=1e-13)
+
+
+def test_uniform_eigenstrain_is_a_shift_of_the_mean_strain():
+    """A uniform eigenstrain E0 solves like the mean strain E_bar - E0 shifted by E0:
+    eps(E_bar; E_* = E0) = eps(E_bar - E0) + E0, with the same stresses, iterate by iterate."""
+    lam, mu = M.random_field(6, 5, 4, seed=3)
+    E = np.array([0.01, -0.003, 0.002, 0.004, 0.0, -0.001])
+    E0 = np.array([0.002, 0.001, -0.004, 0.0, 0.003, 0.001])
+    es = np.broadcast_to(E0[:, None, None, None], (6, 4, 5, 6)).copy()
+    for scheme in ("AFB_R", "CD"):
+        a = O.solve(lam, mu, scheme, E, estar=es, max_iters_exact=6)
+        b = O.solve(lam, mu, scheme, E - E0, max_iters_exact=6)
+        np.testing.assert_allclose(a.eps, b.eps + E0[:, None, None, None], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(a.sigma_mean, b.sigma_mean, rtol=1e-13, atol=1e-15)
+
+
 def _load_golden_1d():
     rows = np.loadtxt(os.path.join(HERE, "golden", "mi1d_sharp.txt"))
     out = {}
