@@ -97,6 +97,16 @@ int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_gri
  * (Sec. 4: C_H = 1/2 (C_M + C_I)).  mu must be > 0 and finite, lambda finite. */
 int gfp_set_phases(gfp_grid g, const double* lambda, const double* mu, int where, const double* ref_lambda_mu);
 
+/* Eigenstrain field E_* (the generalization stated at the end of Sec. 6: T = C[E - E_*], so that the
+ * initial stress becomes T^(0) = C_i[E_bar - E_*i]): [6][n3][n2][n1] float64 tensor components
+ * (11,22,33,23,13,12, no factor 2) sampled like lambda and mu; where = 0 host, 1 device (copied; the
+ * caller keeps ownership).  NULL removes it.  It applies to gfp_solve in FP64 and mixed precision (the
+ * FP64 stress of every outer pass; the FP32 correction equation does not involve it); the strain
+ * returned stays the total strain.  While one is set, the DGO scheme, gfp_effective_stiffness,
+ * gfp_grad and gfp_solve_batch return GFP_ERR_UNSUPPORTED (their results are defined for the
+ * stiffness-only problem). */
+int gfp_set_eigenstrain(gfp_grid g, const double* estar, int where);
+
 /* Solve for the strain with prescribed mean E_macro (6 tensor components) until eta < tol or
  * maxit iterations.  The result's fields are filled even when the status is NOT_CONVERGED. */
 int gfp_solve(gfp_grid g, const gfp_scheme* scheme, const double E_macro[6], double tol, int maxit,

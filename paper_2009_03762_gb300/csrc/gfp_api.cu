@@ -402,6 +402,8 @@ struct gfp_grid_s {
   double* dgo = nullptr;
   double dgo_key[4] = {0, 0, 0, 0};  // lambda_H, mu_H, m, valid
   double* xpart = nullptr;           // per-CTA partials of the x-pass (DGO residual), n2 n3 entries
+  double* estar = nullptr;           // eigenstrain [6][N] while one is set (gfp_set_eigenstrain)
+  bool estar_on = false;
 };
 
 
@@ -578,7 +580,7 @@ void free_grid(gfp_grid g) {
   cudaFree(g->lam32); cudaFree(g->mu32); cudaFree(g->eps32); cudaFree(g->vsrc);
   for (int r = 0; r < 3; ++r) { cudaFree(g->tw32[r]); cudaFree(g->tabA32[r]); cudaFree(g->tabB32[r]); }
   cudaFree(g->st_in); cudaFree(g->cmean); cudaFree(g->cpart);
-  cudaFree(g->dgo); cudaFree(g->xpart);
+  cudaFree(g->dgo); cudaFree(g->xpart); cudaFree(g->estar);
   if (g->st_host) cudaFreeHost(g->st_host);
   if (g->st_in_host) cudaFreeHost(g->st_in_host);
   delete g;
@@ -614,10 +616,21 @@ int ensure_hist(gfp_grid g, int cap) {
   return GFP_OK;
 }
 
+// x-pass parameters of the FP64 passes: the eigenstrain while one is set
+PolarParams fp64_xparams(gfp_grid g) {
+  PolarParams pp;
+  for (int c = 0; c < 6; ++c) pp.E[c] = 0;
+  pp.lam_h = pp.mu_h = 0;
+  pp.partials = nullptr;
+  pp.estar = g->estar_on ? g->estar : nullptr;
+  return pp;
+}
+
 void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta) {
   const Dims& d = g->d;
+  const PolarParams pp = fp64_xparams(g);
   Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
-                         have_delta ? PX_DELTA : 0, nullptr, nullptr, g->st);
+                         have_delta ? PX_DELTA : 0, nullptr, nullptr, g->st, &pp);
   Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
   Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
                          nullptr);
@@ -740,8 +753,9 @@ GammaParams<R> gamma_params(gfp_grid g, int op, const R* const* A, const R* cons
 // exact FP64 residual and mean stress, and v = T kt stored as the inner iterations' source.
 void residual_pass64(gfp_grid g, const GammaParams<double>& gp, bool with_corr) {
   const Dims& d = g->d;
+  const PolarParams pp = fp64_xparams(g);
   Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0,
-                         with_corr ? g->eps32 : nullptr, g->cmean, g->st);
+                         with_corr ? g->eps32 : nullptr, g->cmean, g->st, &pp);
   Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
   Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_RESIDUAL,
                          g->vsrc);
@@ -938,6 +952,7 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   pp.lam_h = g->lam_h;
   pp.mu_h = g->mu_h;
   pp.partials = g->xpart;
+  pp.estar = nullptr;
   const double en2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + 2.0 * (E[3] * E[3] + E[4] * E[4] + E[5] * E[5]);
   const double enorm = std::sqrt(en2) * std::sqrt((double)d.N);
   fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, d.N, E[0], E[1],
@@ -1214,6 +1229,7 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   for (int c = 0; c < 6; ++c) if (!std::isfinite(E[c])) return GFP_ERR_ARG;
   if (!g->phases) return GFP_ERR_ARG;
   if (sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
+  if (g->estar_on && sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
   if (sc->prec == GFP_MIXED) {
     g->resume_pending = false;
     return solve_mixed(g, sc, E, tol, maxit, out);
@@ -1227,6 +1243,21 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   return solve_fp64(g, sc, E, tol, maxit, out, resume);
 }
 
+int gfp_set_eigenstrain(gfp_grid g, const double* estar, int where) {
+  if (!g || (where != 0 && where != 1)) return GFP_ERR_ARG;
+  if (!estar) {
+    g->estar_on = false;
+    return GFP_OK;
+  }
+  const size_t bytes = sizeof(double) * 6 * (size_t)g->d.N;
+  if (!g->estar) GFP_CU(cudaMalloc(&g->estar, bytes));
+  GFP_CU(cudaMemcpyAsync(g->estar, estar, bytes, where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                         g->stream));
+  GFP_CU(cudaStreamSynchronize(g->stream));
+  g->estar_on = true;
+  return GFP_OK;
+}
+
 int gfp_get_strain(gfp_grid g, double* dst, int where) {
   if (!g || !dst || (where != 0 && where != 1)) return GFP_ERR_ARG;
   GFP_CU(cudaMemcpyAsync(dst, g->eps, sizeof(double) * 6 * g->d.N,
@@ -1237,6 +1268,7 @@ int gfp_get_strain(gfp_grid g, double* dst, int where) {
 
 int gfp_effective_stiffness(gfp_grid g, const gfp_scheme* sc, double tol, int maxit, double C_eff[36], int iters[6]) {
   if (!g || !scheme_ok(sc) || !C_eff || maxit < 1) return GFP_ERR_ARG;
+  if (g->estar_on) return GFP_ERR_UNSUPPORTED;
   int worst = GFP_OK;
   for (int J = 0; J < 6; ++J) {
     double E[6] = {0, 0, 0, 0, 0, 0};
@@ -1255,6 +1287,7 @@ int gfp_effective_stiffness(gfp_grid g, const gfp_scheme* sc, double tol, int ma
 int gfp_grad(gfp_grid g, const gfp_scheme* sc, int I, int J, double tol, int maxit, double* dl, double* dm, int where) {
   if (!g || !scheme_ok(sc) || I < 0 || I > 5 || J < 0 || J > 5 || !dl || !dm || (where != 0 && where != 1))
     return GFP_ERR_ARG;
+  if (g->estar_on) return GFP_ERR_UNSUPPORTED;
   const long long N = g->d.N;
   if (!g->eps_save) GFP_CU(cudaMalloc(&g->eps_save, sizeof(double) * 6 * N));
   double E[6] = {0, 0, 0, 0, 0, 0};
@@ -1745,6 +1778,8 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
     return GFP_ERR_UNSUPPORTED;
   for (int i = 0; i < count; ++i)
     if (!grids[i] || !grids[i]->phases) return GFP_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (grids[i]->estar_on) return GFP_ERR_UNSUPPORTED;
   // shared per-grid data: FP32 Lame fields, tables, twiddles
   for (int i = 0; i < count; ++i) {
     gfp_grid g = grids[i];

@@ -604,7 +604,12 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
     }
     T zz[3];
     if (polar) pack_stress<R>(e, lu[u] - (R)pp.lam_h, mu_[u] - (R)pp.mu_h, zz);
-    else pack_stress<R>(e, lu[u], mu_[u], zz);
+    else if (pp.estar) {
+      R es[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) es[c] = e[c] - (R)pp.estar[c * d.N + vv];
+      pack_stress<R>(es, lu[u], mu_[u], zz);
+    } else pack_stress<R>(e, lu[u], mu_[u], zz);
 #pragma unroll
     for (int q = 0; q < 3; ++q) buf[(q * lines + ll) * LP + px] = zz[q];
     }

@@ -168,10 +168,13 @@ enum { PX_DELTA = 1, PX_ZERO = 2, PX_POLAR = 4 };
 // Eloh2019): with PX_POLAR the x-pass forms eps = E_bar + inverse transform (instead of adding it),
 // accumulates ||eps_new - eps_old||_F^2 per CTA into partials[blockIdx.x] when PX_DELTA is set, and
 // transforms tau = (C - C_H) : eps instead of sigma = C : eps.
+// estar (eigenstrain generalization at the end of Sec. 6, FP64 passes): if set, the stress is
+// sigma = C : (eps - estar), estar [6][N] in the strain's layout; the stored strain stays total.
 struct PolarParams {
   double E[6];
   double lam_h, mu_h;
   double* partials;
+  const double* estar;
 };
 
 // Stress (or polarization) of one voxel, packed as the three complex pairs (11,22), (33,23), (13,12).
@@ -309,7 +312,12 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
     }
     T zz[3];
     if (polar) pack_stress<R>(e, lam[v] - (R)pp.lam_h, mu[v] - (R)pp.mu_h, zz);
-    else pack_stress<R>(e, lam[v], mu[v], zz);
+    else if (pp.estar) {
+      R es[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) es[c] = e[c] - (R)pp.estar[c * d.N + v];
+      pack_stress<R>(es, lam[v], mu[v], zz);
+    } else pack_stress<R>(e, lam[v], mu[v], zz);
 #pragma unroll
     for (int p = 0; p < 3; ++p) buf[(p * lines + l) * n1 + x] = zz[p];
   }

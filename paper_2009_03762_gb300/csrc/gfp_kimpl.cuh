@@ -75,7 +75,7 @@ inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>:
                        const R* mu, const typename C<R>::T* tw, const Dims& d, int flags, const float* corr,
                        const double* corr_mean, const PolarParams& pp, const SolveState* st) {
   typedef typename C<R>::T T;
-  if (async && !(flags & PX_POLAR)) {
+  if (async && !(flags & PX_POLAR) && !pp.estar) {
     int lines = want_lines > 0 ? want_lines : 2;
     lines = std::min(lines, 512 / (3 * CPlan<N>::T));
     while (lines > 1 && xa_smem_bytes<R, N>(lines) > 200 * 1024) --lines;
@@ -99,7 +99,12 @@ void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, con
                        const SolveState* st, const PolarParams* ppp) {
   PolarParams pp;
   if (ppp) pp = *ppp;
-  else { for (int c = 0; c < 6; ++c) pp.E[c] = 0; pp.lam_h = pp.mu_h = 0; pp.partials = nullptr; }
+  else {
+    for (int c = 0; c < 6; ++c) pp.E[c] = 0;
+    pp.lam_h = pp.mu_h = 0;
+    pp.partials = nullptr;
+    pp.estar = nullptr;
+  }
   switch (d.n1) {
 #define GFP_CASE(N) \
     case N: launch_x_c<R, N>(s, lc.cx_lines, lc.x_async, spec, eps, lam, mu, tw, d, flags, corr, corr_mean, pp, st); return;

@@ -45,7 +45,7 @@ _lib = None
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
            "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
-           "gfp_solve_batch", "gfp_set_fault_injection")
+           "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain")
 
 
 def lib():
@@ -76,6 +76,7 @@ def lib():
     L.gfp_solve_batch.argtypes = [ip, vp, ctypes.POINTER(Scheme), dp, ip, vp, vp]
     L.gfp_set_fault_injection.argtypes = [ip, ip]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
+    L.gfp_set_eigenstrain.argtypes = [vp, vp, ip]
     L.gfp_last_error_detail.argtypes = []
     L.gfp_last_error_detail.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -168,6 +169,20 @@ class Grid:
             self._ref = (ctypes.c_double * 2)(float(ref[0]), float(ref[1]))
             refp = ctypes.cast(self._ref, ctypes.c_void_p)
         _check(lib().gfp_set_phases(self._h, pl, pm, wl, refp), "gfp_set_phases")
+
+    def set_eigenstrain(self, estar):
+        """Eigenstrain field [6, n3, n2, n1] float64 (numpy or torch), or None to remove it; the stress
+        becomes C : (eps - estar)."""
+        if estar is None:
+            _check(lib().gfp_set_eigenstrain(self._h, None, 0), "gfp_set_eigenstrain")
+            return
+        if isinstance(estar, np.ndarray):
+            estar = np.ascontiguousarray(estar, dtype=np.float64)
+        count = estar.size if isinstance(estar, np.ndarray) else estar.numel()
+        if count != 6 * int(np.prod(self.shape)):
+            raise ValueError("eigenstrain must hold 6 x n3 x n2 x n1 values")
+        p, w = _ptr_where(estar)
+        _check(lib().gfp_set_eigenstrain(self._h, p, w), "gfp_set_eigenstrain")
 
     def solve(self, sch, E, tol=1e-8, maxit=1000, history=False, raise_on_error=False):
         E = (ctypes.c_double * 6)(*[float(v) for v in E])
