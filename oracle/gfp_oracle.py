@@ -340,8 +340,9 @@ def dgo_apply(Gc, A):
 # Algorithms T-3D / P-3D / D-3D
 # --------------------------------------------------------------------------------------
 class Result:
-    def __init__(self, eps, iters, residual, history, sigma_mean, converged):
+    def __init__(self, eps, iters, residual, history, sigma_mean, converged, disp=None):
         self.eps = eps                  # (6, n3, n2, n1) tensor components (11,22,33,23,13,12)
+        self.disp = disp                # (3, n3, n2, n1) periodic displacement u^p = F^+ u_check (Alg. T/P)
         self.iters = iters
         self.residual = residual
         self.history = history
@@ -411,7 +412,9 @@ def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=
         u = u + du
         du_prev = du
     sig_mean = tensor_to_voigt(T.mean(axis=(-3, -2, -1)))
-    return Result(tensor_to_voigt(eps), it, history[-1], history, sig_mean, bool(converged))
+    # the displacement coefficients u_check that produced eps (the last increment is not added at exit)
+    disp = inverse3(u, mats).real
+    return Result(tensor_to_voigt(eps), it, history[-1], history, sig_mean, bool(converged), disp)
 
 
 def _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_table, max_iters_exact,

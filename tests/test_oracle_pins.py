@@ -312,6 +312,63 @@ def test_uniform_eigenstrain_is_a_shift_of_the_mean_strain():
         np.testing.assert_allclose(a.sigma_mean, b.sigma_mean, rtol=1e-13, atol=1e-15)
 
 
+def _sym_grad_spectral(disp, symbols):
+    """sym(grad u) with per-axis difference symbols applied by numpy's FFT: symbols[r] is a function of
+    (theta1, theta2, theta3) on the FFT grid giving the symbol of the derivative along x_(r+1)."""
+    n3, n2, n1 = disp.shape[1:]
+    t3, t2, t1 = np.meshgrid(*[2 * np.pi * np.fft.fftfreq(n) for n in (n3, n2, n1)], indexing="ij")
+    uh = [np.fft.fftn(disp[i]) for i in range(3)]
+    q = [symbols[r](t1, t2, t3) for r in range(3)]
+    G = np.empty((3, 3, n3, n2, n1))
+    for i in range(3):
+        for j in range(3):
+            G[i, j] = np.fft.ifftn(q[j] * uh[i]).real       # d u_i / d x_j
+    return 0.5 * (G + G.transpose(1, 0, 2, 3, 4))
+
+
+def _afd_symbols():
+    """AFD (eq. FreDifFinFBDF3D): forward difference along r averaged (e^{i theta} + 1)/2 over the
+    other two axes."""
+    fd = lambda t: np.exp(1j * t) - 1.0
+    av = lambda t: 0.5 * (np.exp(1j * t) + 1.0)
+    return [lambda t1, t2, t3: fd(t1) * av(t2) * av(t3),
+            lambda t1, t2, t3: fd(t2) * av(t3) * av(t1),
+            lambda t1, t2, t3: fd(t3) * av(t1) * av(t2)]
+
+
+def test_displacement_afb_r_reproduces_strain_3d():
+    """The displacement u^p = F^+ u_check of Algorithm T with AFB/R: its AFD difference gives back the
+    strain fluctuation exactly (any grid), sym(q^AFD (x) u) = eps - E_bar."""
+    lam, mu = M.random_field(6, 5, 4, seed=6)
+    E = np.array([0.01, -0.004, 0.002, 0.003, -0.002, 0.001])
+    r = O.solve(lam, mu, "AFB_R", E, tol=1e-11, maxit=2000)
+    S = _sym_grad_spectral(r.disp, _afd_symbols())
+    Ef = O.voigt_to_tensor(r.eps) - O.voigt_to_tensor(E)[:, :, None, None, None]
+    np.testing.assert_allclose(S, Ef, rtol=0, atol=1e-14)
+    assert abs(r.disp.mean()) < 1e-16
+
+
+@pytest.mark.parametrize("scheme", ["F", "AHC", "ACD"])
+def test_displacement_reproduces_strain_odd_grid(scheme):
+    """Schemes without the half-voxel phase: on odd grids (no Nyquist mode) sym(q^a (x) u^p) gives back
+    the strain fluctuation; q^a = i k (F), i 2 sin(theta/2) cos cos (AHC), i sin(theta) cos cos (ACD)."""
+    lam, mu = M.random_field(5, 7, 3, seed=8)
+    E = np.array([0.01, -0.004, 0.002, 0.003, -0.002, 0.001])
+    r = O.solve(lam, mu, scheme, E, tol=1e-11, maxit=4000)
+    if scheme == "F":
+        f, a = (lambda t: 1j * t), (lambda t: 1.0)
+    elif scheme == "AHC":
+        f, a = (lambda t: 2j * np.sin(0.5 * t)), (lambda t: np.cos(0.5 * t))
+    else:
+        f, a = (lambda t: 1j * np.sin(t)), (lambda t: np.cos(t))
+    sym = [lambda t1, t2, t3: f(t1) * a(t2) * a(t3),
+           lambda t1, t2, t3: f(t2) * a(t3) * a(t1),
+           lambda t1, t2, t3: f(t3) * a(t1) * a(t2)]
+    S = _sym_grad_spectral(r.disp, sym)
+    Ef = O.voigt_to_tensor(r.eps) - O.voigt_to_tensor(E)[:, :, None, None, None]
+    np.testing.assert_allclose(S, Ef, rtol=0, atol=1e-13)
+
+
 def _load_golden_1d():
     rows = np.loadtxt(os.path.join(HERE, "golden", "mi1d_sharp.txt"))
     out = {}
