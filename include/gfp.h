@@ -107,6 +107,17 @@ int gfp_set_phases(gfp_grid g, const double* lambda, const double* mu, int where
  * stiffness-only problem). */
 int gfp_set_eigenstrain(gfp_grid g, const double* estar, int where);
 
+/* Periodic displacement of the last solve, u^p = F^+ u_check, the primary unknown of Algorithms T/P
+ * (Sec. 5.2, 5.4): recovered mode by mode from the strain fluctuation E~ = sym(u_check (x) q^a) with
+ * the scheme's q^a (pass the scheme of the solve): u_check = (2 E~ kt - kt (kt.E~ kt)/|kt|^2) / (c i |kt|^2),
+ * c = 1 except for AFB/R (c = e^{i(theta1+theta2+theta3)/2}, the forward difference's half-voxel
+ * shift), 0 where kt = 0.  dst: [3][n3][n2][n1] float64 (where = 0 host, 1 device), zero mean; the
+ * total displacement is E_bar x + u^p.  On Nyquist planes of even axes the schemes without the phase
+ * (F, CD, ACD, HC, AHC) have a purely imaginary q^a, whose real displacement vanishes there: those
+ * strain modes are not represented.  GFP_ERR_ARG before any solve; DGO returns GFP_ERR_UNSUPPORTED.
+ * The grid's spectrum buffer is used as scratch; the strain is not changed. */
+int gfp_get_displacement(gfp_grid g, const gfp_scheme* scheme, double* dst, int where);
+
 /* Solve for the strain with prescribed mean E_macro (6 tensor components) until eta < tol or
  * maxit iterations.  The result's fields are filled even when the status is NOT_CONVERGED. */
 int gfp_solve(gfp_grid g, const gfp_scheme* scheme, const double E_macro[6], double tol, int maxit,

@@ -404,6 +404,8 @@ struct gfp_grid_s {
   double* xpart = nullptr;           // per-CTA partials of the x-pass (DGO residual), n2 n3 entries
   double* estar = nullptr;           // eigenstrain [6][N] while one is set (gfp_set_eigenstrain)
   bool estar_on = false;
+  double E_last[6] = {0, 0, 0, 0, 0, 0};  // mean strain of the last solve (displacement output)
+  bool have_solution = false;
 };
 
 
@@ -746,6 +748,8 @@ GammaParams<R> gamma_params(gfp_grid g, int op, const R* const* A, const R* cons
   gp.c_lm = (R)((g->lam_h + g->mu_h) / (g->mu_h * (g->lam_h + 2.0 * g->mu_h)));
   gp.invN = (R)(1.0 / (double)g->d.N);
   gp.nyq_avg = (op == OP_F || op == OP_HC) ? 1 : 0;
+  gp.half_shift = (op == OP_AFB_R) ? 1 : 0;
+  gp.dgo = nullptr;
   return gp;
 }
 
@@ -1230,6 +1234,8 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   if (!g->phases) return GFP_ERR_ARG;
   if (sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
   if (g->estar_on && sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
+  for (int c = 0; c < 6; ++c) g->E_last[c] = E[c];
+  g->have_solution = true;
   if (sc->prec == GFP_MIXED) {
     g->resume_pending = false;
     return solve_mixed(g, sc, E, tol, maxit, out);
@@ -1255,6 +1261,43 @@ int gfp_set_eigenstrain(gfp_grid g, const double* estar, int where) {
                          g->stream));
   GFP_CU(cudaStreamSynchronize(g->stream));
   g->estar_on = true;
+  return GFP_OK;
+}
+
+int gfp_get_displacement(gfp_grid g, const gfp_scheme* sc, double* dst, int where) {
+  if (!g || !scheme_ok(sc) || !dst || (where != 0 && where != 1)) return GFP_ERR_ARG;
+  if (!g->have_solution) return GFP_ERR_ARG;
+  if (sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
+  int rc = ensure_tables(g, sc->op);
+  if (rc) return rc;
+  const Dims& d = g->d;
+  const size_t bytes = sizeof(double) * 3 * (size_t)d.N;
+  double* out = reinterpret_cast<double*>(dst);
+  if (where == 0) {
+    if (!g->eps_save) GFP_CU(cudaMalloc(&g->eps_save, sizeof(double) * 6 * (size_t)d.N));
+    out = g->eps_save;
+  }
+  const GammaParams<double> gp = gamma_params<double>(g, sc->op, g->tabA, g->tabB);
+  PolarParams pp = fp64_xparams(g);
+  pp.estar = nullptr;
+  for (int c = 0; c < 6; ++c) pp.E[c] = g->E_last[c];
+  SolveState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.maxit = 1 << 30;
+  *g->st_host = s0;
+  GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
+  // forward transform of eps - E_bar, u^ per mode, inverse transform of its 3 components
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_STRAIN,
+                         nullptr, nullptr, g->st, &pp);
+  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_DISP,
+                         nullptr);
+  Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, out, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+                         PX_DELTA | PX_OUTPUT, nullptr, nullptr, g->st, &pp);
+  GFP_CU(cudaGetLastError());
+  if (where == 0) GFP_CU(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, g->stream));
+  GFP_CU(cudaStreamSynchronize(g->stream));
   return GFP_OK;
 }
 

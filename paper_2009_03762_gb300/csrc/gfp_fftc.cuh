@@ -226,6 +226,13 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
       const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
       const bool ny3 = (2 * z == N);
       const long long vi = d.row(z, k2) * d.P + k1;
+      if (mode == PZ_DISP) {
+        T o[6];
+        disp_point<R>(tt, kt1, kt2, kt3, gp.half_shift, d, k1, k2, z, gp.invN, o);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rowz[(c * cols + cc) ^ sw] = o[c];
+        continue;
+      }
       if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) st->T0[c] = (double)tt[c].x;
@@ -515,6 +522,7 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
   const bool live = (fl < 3 * lines) && (li < nlines);
   const bool zero = (flags & PX_ZERO) != 0 || st->restart;
   const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
+  const bool outmode = (flags & PX_OUTPUT) != 0, strainmode = (flags & PX_STRAIN) != 0;
   const SLine<T, true> sl{buf + fl * LP, 1};
   T v[P::E];
   if (have_delta) {
@@ -565,7 +573,7 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
       const bool ok = i < nvox && lj < nlines;
       const long long vv = lj * N + i % N;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) eu[u][c] = (ok && !zero) ? eps[c * d.N + vv] : (R)0;
+      for (int c = 0; c < 6; ++c) eu[u][c] = (ok && !zero && !outmode) ? eps[c * d.N + vv] : (R)0;
       lu[u] = ok ? lam[vv] : (R)0;
       mu_[u] = ok ? mu[vv] : (R)0;
     }
@@ -588,6 +596,11 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
         dd[2 * q] = z.x;
         dd[2 * q + 1] = z.y;
       }
+      if (outmode) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) eps[c * d.N + vv] = dd[c];
+        continue;
+      }
       if (polar) dacc += polar_update<R>(e, dd, pp);
       else {
 #pragma unroll
@@ -603,7 +616,11 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
       for (int c = 0; c < 6; ++c) eps[c * d.N + vv] = e[c];
     }
     T zz[3];
-    if (polar) pack_stress<R>(e, lu[u] - (R)pp.lam_h, mu_[u] - (R)pp.mu_h, zz);
+    if (strainmode) {
+      zz[0].x = e[0] - (R)pp.E[0]; zz[0].y = e[1] - (R)pp.E[1];
+      zz[1].x = e[2] - (R)pp.E[2]; zz[1].y = e[3] - (R)pp.E[3];
+      zz[2].x = e[4] - (R)pp.E[4]; zz[2].y = e[5] - (R)pp.E[5];
+    } else if (polar) pack_stress<R>(e, lu[u] - (R)pp.lam_h, mu_[u] - (R)pp.mu_h, zz);
     else if (pp.estar) {
       R es[6];
 #pragma unroll
@@ -614,6 +631,7 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
     for (int q = 0; q < 3; ++q) buf[(q * lines + ll) * LP + px] = zz[q];
     }
   }
+  if (outmode) return;
   if (polar && have_delta) {
     const double sum = block_sum(dacc, red);
     if (threadIdx.x == 0) pp.partials[blockIdx.x] = sum;

@@ -61,6 +61,7 @@ struct GammaParams {
   R c_lm;              // (lambda_H + mu_H) / (mu_H (lambda_H + 2 mu_H))
   R invN;
   int nyq_avg;         // average Gamma over the Hermitian partner on Nyquist planes (F, HC)
+  int half_shift;      // displacement recovery: q^a = e^{i (th1 + th2 + th3)/2} i kt (AFB/R), else i kt
   const double* dgo;   // DGO: 21 Mandel entries per half-spectrum point, [21][k3][k2][P] (mode PZ_DGO)
 };
 
@@ -162,7 +163,10 @@ __device__ __forceinline__ R tk_norm2(const T t[6], R k1, R k2, R k3) {
 // --------------------------------------------------------------------------------------------
 // pass_x: one CTA handles `lines` consecutive x1-lines (fixed i3, consecutive i2).
 // --------------------------------------------------------------------------------------------
-enum { PX_DELTA = 1, PX_ZERO = 2, PX_POLAR = 4 };
+// PX_STRAIN: transform the strain fluctuation eps - E (pp.E) instead of the stress (no state update).
+// PX_OUTPUT (with PX_DELTA): write the inverse transform of components 0-2 to `eps`, here a [3][N]
+// output array, and stop (displacement output).
+enum { PX_DELTA = 1, PX_ZERO = 2, PX_POLAR = 4, PX_STRAIN = 8, PX_OUTPUT = 16 };
 
 // Polarization form of the discrete-Green-operator iteration (Algorithm D with the polarization of
 // Eloh2019): with PX_POLAR the x-pass forms eps = E_bar + inverse transform (instead of adding it),
@@ -237,6 +241,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
   const long long line0 = (long long)blockIdx.x * lines;
   const bool zero = (flags & PX_ZERO) != 0 || st->restart;
   const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
+  const bool outmode = (flags & PX_OUTPUT) != 0, strainmode = (flags & PX_STRAIN) != 0;
   for (int i = threadIdx.x; i < n1; i += blockDim.x) twl[i] = tw[i];
   const int tot_lines = 3 * lines;
   if (have_delta) {
@@ -281,7 +286,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
     if (li >= nlines) continue;
     const long long v = li * n1 + x;
     R e[6];
-    if (zero) {
+    if (zero || outmode) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) e[c] = (R)0;
     } else {
@@ -295,6 +300,11 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
         const T z = buf[(p * lines + l) * n1 + x];
         dd[2 * p] = z.x;
         dd[2 * p + 1] = z.y;
+      }
+      if (outmode) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) eps[c * d.N + v] = dd[c];
+        continue;
       }
       if (polar) dacc += polar_update<R>(e, dd, pp);
       else {
@@ -311,7 +321,11 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
       for (int c = 0; c < 6; ++c) eps[c * d.N + v] = e[c];
     }
     T zz[3];
-    if (polar) pack_stress<R>(e, lam[v] - (R)pp.lam_h, mu[v] - (R)pp.mu_h, zz);
+    if (strainmode) {
+      zz[0].x = e[0] - (R)pp.E[0]; zz[0].y = e[1] - (R)pp.E[1];
+      zz[1].x = e[2] - (R)pp.E[2]; zz[1].y = e[3] - (R)pp.E[3];
+      zz[2].x = e[4] - (R)pp.E[4]; zz[2].y = e[5] - (R)pp.E[5];
+    } else if (polar) pack_stress<R>(e, lam[v] - (R)pp.lam_h, mu[v] - (R)pp.mu_h, zz);
     else if (pp.estar) {
       R es[6];
 #pragma unroll
@@ -321,6 +335,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
 #pragma unroll
     for (int p = 0; p < 3; ++p) buf[(p * lines + l) * n1 + x] = zz[p];
   }
+  if (outmode) return;
   if (polar && have_delta) {
     const double sum = block_sum(dacc, red);
     if (threadIdx.x == 0) pp.partials[blockIdx.x] = sum;
@@ -382,7 +397,50 @@ __global__ void pass_y_kernel(typename C<R>::T* __restrict__ spec, const typenam
 // pass_z_gamma: tile = all n3 rows x `cols` k1 columns x 6 components at fixed k2.
 // smem layout [k3][comp][col] so that line (comp, col) has element stride 6 cols.
 // --------------------------------------------------------------------------------------------
-enum { PZ_GAMMA = 0, PZ_RESIDUAL = 1, PZ_INNER = 2, PZ_DGO = 3 };
+enum { PZ_GAMMA = 0, PZ_RESIDUAL = 1, PZ_INNER = 2, PZ_DGO = 3, PZ_DISP = 4 };
+
+// mode PZ_DISP (displacement output, FP64): the tile holds the transformed strain fluctuation
+// E~(k) = sym(u^(k) (x) q^a(k)) of a solution; it is replaced by u^(k) / N in components 0-2 (3-5 zeroed).
+// With q^a = c i kt, |c| = 1: sym(u (x) kt) = E~ / (c i), so u = (2 E~ kt - kt (kt.E~ kt)/|kt|^2) / (c i |kt|^2);
+// u = 0 where kt = 0 (as the Green operator there).
+__device__ __forceinline__ double disp_theta(int i, int n) {
+  const int kap = (i < (n + 1) / 2) ? i : i - n;  // the Nyquist index of an even axis is kappa = -n/2
+  return 6.283185307179586476925286766559 * (double)kap / (double)n;
+}
+template <typename R, typename T>
+__device__ __forceinline__ void disp_point(const T t[6], R k1, R k2, R k3, int half_shift, const Dims& d, int i1,
+                                           int i2, int i3, R invN, T o[6]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) { o[c].x = 0; o[c].y = 0; }
+  const R s = k1 * k1 + k2 * k2 + k3 * k3;
+  if (s == (R)0) return;
+  T v1, v2, v3;
+  tk_vec<R>(t, k1, k2, k3, v1, v2, v3);
+  T kv;
+  kv.x = k1 * v1.x + k2 * v2.x + k3 * v3.x;
+  kv.y = k1 * v1.y + k2 * v2.y + k3 * v3.y;
+  const R is = (R)1 / s;
+  T nn[3];
+  nn[0].x = 2 * v1.x - k1 * kv.x * is; nn[0].y = 2 * v1.y - k1 * kv.y * is;
+  nn[1].x = 2 * v2.x - k2 * kv.x * is; nn[1].y = 2 * v2.y - k2 * kv.y * is;
+  nn[2].x = 2 * v3.x - k3 * kv.x * is; nn[2].y = 2 * v3.y - k3 * kv.y * is;
+  // divide by c i: multiply by -i conj(c) = -ci - i cr  (c = cr + i ci)
+  R cr = 1, ci = 0;
+  if (half_shift) {
+    const double ph = 0.5 * (disp_theta(i1, d.n1) + disp_theta(i2, d.n2) + disp_theta(i3, d.n3));
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    cr = (R)cs;
+    ci = (R)sn;
+  }
+  const R f = is * invN;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    // (x + i y) (-ci - i cr) = (y cr - x ci) + i (-x cr - y ci)
+    o[c].x = f * (nn[c].y * cr - nn[c].x * ci);
+    o[c].y = -f * (nn[c].x * cr + nn[c].y * ci);
+  }
+}
 
 // mode PZ_GAMMA: Delta E = -Gamma0(kt) T / N, residual, T(0), inverse z (the FP64 or FP32 iteration).
 // mode PZ_RESIDUAL: residual and T(0) only; stores v = T kt (FP32, [3][k3][k2][P]) as the source of
@@ -431,6 +489,13 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
     const bool ny3 = ((d.n3 & 1) == 0) && (2 * z == d.n3);
     const bool self1 = (k1 == 0) || ny1;
     const long long vi = d.row(z, k2) * d.P + k1;
+    if (mode == PZ_DISP) {
+      T o[6];
+      disp_point<R>(t, kt1, kt2, kt3, gp.half_shift, d, k1, k2, z, gp.invN, o);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+      continue;
+    }
     if (mode != PZ_INNER && k1 == 0 && k2 == 0 && z == 0) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) st->T0[c] = (double)t[c].x;

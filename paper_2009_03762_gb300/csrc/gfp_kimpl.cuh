@@ -75,7 +75,7 @@ inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>:
                        const R* mu, const typename C<R>::T* tw, const Dims& d, int flags, const float* corr,
                        const double* corr_mean, const PolarParams& pp, const SolveState* st) {
   typedef typename C<R>::T T;
-  if (async && !(flags & PX_POLAR) && !pp.estar) {
+  if (async && !(flags & (PX_POLAR | PX_STRAIN | PX_OUTPUT)) && !pp.estar) {
     int lines = want_lines > 0 ? want_lines : 2;
     lines = std::min(lines, 512 / (3 * CPlan<N>::T));
     while (lines > 1 && xa_smem_bytes<R, N>(lines) > 200 * 1024) --lines;
@@ -154,7 +154,7 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
     case N: {                                                                                                 \
       const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
       const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols) + 128;                                 \
-      if (mode != PZ_DGO && lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 &&        \
+      if (mode != PZ_DGO && mode != PZ_DISP && lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 &&        \
           smt <= 220 * 1024) {                    \
         const int ntiles = ntx * d.n2;                                                                        \
         const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \

@@ -45,7 +45,7 @@ _lib = None
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
            "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
-           "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain")
+           "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain", "gfp_get_displacement")
 
 
 def lib():
@@ -77,6 +77,7 @@ def lib():
     L.gfp_set_fault_injection.argtypes = [ip, ip]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
     L.gfp_set_eigenstrain.argtypes = [vp, vp, ip]
+    L.gfp_get_displacement.argtypes = [vp, ctypes.POINTER(Scheme), vp, ip]
     L.gfp_last_error_detail.argtypes = []
     L.gfp_last_error_detail.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -183,6 +184,17 @@ class Grid:
             raise ValueError("eigenstrain must hold 6 x n3 x n2 x n1 values")
         p, w = _ptr_where(estar)
         _check(lib().gfp_set_eigenstrain(self._h, p, w), "gfp_set_eigenstrain")
+
+    def displacement(self, sch, out=None):
+        """Periodic displacement u^p [3, n3, n2, n1] of the last solve (scheme `sch`, as solved)."""
+        if out is None:
+            out = np.empty((3,) + self.shape)
+        count = out.size if isinstance(out, np.ndarray) else out.numel()
+        if count != 3 * int(np.prod(self.shape)):
+            raise ValueError("displacement output must hold 3 x n3 x n2 x n1 values")
+        p, w = _ptr_where(out)
+        _check(lib().gfp_get_displacement(self._h, ctypes.byref(sch), p, w), "gfp_get_displacement")
+        return out
 
     def solve(self, sch, E, tol=1e-8, maxit=1000, history=False, raise_on_error=False):
         E = (ctypes.c_double * 6)(*[float(v) for v in E])
