@@ -226,7 +226,7 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
       const R kt1 = a1 * b2 * b3, kt2 = a2 * b3 * b1, kt3 = a3 * b1 * b2;
       const bool ny3 = (2 * z == N);
       const long long vi = d.row(z, k2) * d.P + k1;
-      if (mode == PZ_DISP) {
+      if (sizeof(R) == 8 && mode == PZ_DISP) {  // FP64 only (folded out of the FP32 kernels' registers)
         T o[6];
         disp_point<R>(tt, kt1, kt2, kt3, gp.half_shift, d, k1, k2, z, gp.invN, o);
 #pragma unroll
@@ -522,7 +522,10 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
   const bool live = (fl < 3 * lines) && (li < nlines);
   const bool zero = (flags & PX_ZERO) != 0 || st->restart;
   const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
-  const bool outmode = (flags & PX_OUTPUT) != 0, strainmode = (flags & PX_STRAIN) != 0;
+  // eigenstrain and displacement output are FP64 features: compiled out of the FP32 instance, whose
+  // registers (64) set its occupancy
+  constexpr bool F64 = sizeof(R) == 8;
+  const bool outmode = F64 && (flags & PX_OUTPUT) != 0, strainmode = F64 && (flags & PX_STRAIN) != 0;
   const SLine<T, true> sl{buf + fl * LP, 1};
   T v[P::E];
   if (have_delta) {
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
       zz[1].x = e[2] - (R)pp.E[2]; zz[1].y = e[3] - (R)pp.E[3];
       zz[2].x = e[4] - (R)pp.E[4]; zz[2].y = e[5] - (R)pp.E[5];
     } else if (polar) pack_stress<R>(e, lu[u] - (R)pp.lam_h, mu_[u] - (R)pp.mu_h, zz);
-    else if (pp.estar) {
+    else if (F64 && pp.estar) {
       R es[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) es[c] = e[c] - (R)pp.estar[c * d.N + vv];

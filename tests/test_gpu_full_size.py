@@ -71,3 +71,27 @@ def test_bench_cell_256_mixed_matches_fp64(gfp):
     assert _rel(rm.sigma_mean, r64.sigma_mean) <= 1e-6
     assert _rel(eps_m, eps_64) <= 1e-5
     g.close()
+
+
+def test_laminate_512_along_x3_closed_form(gfp):
+    """512^3 (the largest register-FFT length, 134 M voxels), mixed precision with tuned tiles: layers
+    along x3 against the closed-form mean stress."""
+    n = 512
+    rng = np.random.Generator(np.random.PCG64(22))
+    Ey = np.exp(rng.uniform(np.log(0.5), np.log(20.0), size=n))
+    nu = rng.uniform(0.15, 0.4, size=n)
+    l3, m3 = M.lame(Ey, nu)
+    lam = np.broadcast_to(l3[:, None, None], (n, n, n)).copy()
+    mu = np.broadcast_to(m3[:, None, None], (n, n, n)).copy()
+    E = np.array([0.004, -0.002, 0.01, 0.003, -0.002, 0.001])
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu)
+    sch = gfp.scheme("AFB_R", "PCD", "MIXED")
+    g.tune(sch, iters=2)
+    r = g.solve(sch, E, 1e-9, 20000)
+    assert r.converged
+    Mm = l3 + 2 * m3
+    s33 = (E[2] + np.mean(l3 / Mm) * (E[0] + E[1])) / np.mean(1 / Mm)
+    s13 = E[4] / np.mean(1 / (2 * m3))
+    np.testing.assert_allclose([r.sigma_mean[2], r.sigma_mean[4]], [s33, s13], rtol=1e-6)
+    g.close()
