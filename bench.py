@@ -253,9 +253,32 @@ def run_gfp(args, rank=0, world=1, local=0):
                 "d2h_bytes_per_step": 6 * N * 8 / K},
         "gpu_launches": launches,
         "clocks": clk,
+        "cufft_comparison": cufft_comparison(n) if prec == "MIXED" else None,
     }
     g.close()
     return line
+
+
+def cufft_comparison(n, reps=20):
+    """Comparison point only (not on the hot path): cuFFT through torch.fft, R2C + C2R of the six
+    FP32 components of an n^3 field, CUDA events, inputs larger than L2."""
+    import torch
+    x = torch.randn(6, n, n, n, device="cuda", dtype=torch.float32)
+    for _ in range(3):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=(n, n, n), dim=(1, 2, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=(n, n, n), dim=(1, 2, 3))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del x, y
+    torch.cuda.empty_cache()
+    return {"library": "cuFFT via torch.fft", "what": "R2C + C2R of 6 FP32 components, %d^3" % n,
+            "ms": ms, "note": "the solver's FP32 iteration does these transforms plus stress, Green step, "
+                              "residual and update"}
 
 
 def passes_only(args):
@@ -306,6 +329,37 @@ def convergence_experiment(args):
                 print(json.dumps(out[-1]), flush=True)
     g.close()
     return out
+
+
+def schemes128_experiment(args):
+    """All schemes in FP64 on the 128^3 smooth-interface cube (edge 64, tanh of half-width 2 voxels in
+    log-moduli, nu = 0.3), contrasts 1e-3, 1e-1, 10, 1e3, six Voigt unit loads to eta < 1e-10 (DGO:
+    its own residual, m = n/2): inner iterations per load, status and voxel-iterations/s.  TD and PCD
+    give the same iterates for these schemes (the oracle pins it), so PCD is run."""
+    import torch
+    from paper_2009_03762_gb300 import gfp, microstructure as M
+    n = 128
+    g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
+    for chi in (1e-3, 1e-1, 10.0, 1e3):
+        lam, mu = M.smooth_cube(n, 64, chi, width=2.0)
+        g.set_phases(lam, mu)
+        for op in ("F", "CD", "ACD", "HC", "AHC", "AFB_R", "DGO"):
+            maxit = args.schemes_maxit_slow if op in ("F", "HC") else 20000
+            sch = gfp.scheme(op, "PCD", "FP64", dgo_m=n // 2 if op == "DGO" else 0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                C, its, rc = g.effective_stiffness(sch, 1e-10, maxit)
+            except gfp.GfpError as err:
+                print(json.dumps({"chi": chi, "scheme": op, "error": str(err)}), flush=True)
+                continue
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rec = {"chi": chi, "scheme": op, "iters": list(its), "status": gfp.STATUS[rc], "seconds": dt,
+                   "voxel-iterations/s": n ** 3 * float(sum(its)) / dt,
+                   "C1111": float(C[0, 0]), "C1212": float(C[5, 5])}
+            print(json.dumps(rec), flush=True)
+    g.close()
 
 
 def batch_experiment(args):
@@ -428,10 +482,12 @@ def main():
     ap.add_argument("--ttt-maxit", type=int, default=3000)
     ap.add_argument("--tune", type=int, default=1, help="run the tile autotuner before timing")
     ap.add_argument("--tiles", default="", help="x lines,y columns,z columns (negative z: TMA z-pass)")
-    ap.add_argument("--experiment", default="", help="conv3d: iterations vs contrast for the paper's 3D cell; batch: batched homogenization")
+    ap.add_argument("--experiment", default="", help="conv3d: iterations vs contrast for the paper's 3D cell; batch: batched homogenization; "
+                    "schemes128: all schemes on the 128^3 smooth cube")
     ap.add_argument("--conv-tol", type=float, default=1e-8)
     ap.add_argument("--conv-maxit-f", type=int, default=3000)
     ap.add_argument("--batch-count", type=int, default=32)
+    ap.add_argument("--schemes-maxit-slow", type=int, default=3000, help="iteration cap of F and HC in schemes128")
     ap.add_argument("--batch-maxit", type=int, default=20000)
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -453,6 +509,9 @@ def main():
         return
     if args.experiment == "batch":
         print(json.dumps(batch_experiment(args)))
+        return
+    if args.experiment == "schemes128":
+        schemes128_experiment(args)
         return
     rank, world, local = dist_setup()
     line = run_gfp(args, rank, world, local)
