@@ -71,3 +71,18 @@ def test_displacement_errors(gfp):
     with pytest.raises(ValueError):
         g.displacement(gfp.scheme("AFB_R"), out=np.empty((3, 8, 8, 7)))
     g.close()
+
+
+def test_displacement_into_device_memory(gfp):
+    """The displacement written to a CUDA tensor equals the host copy."""
+    torch = pytest.importorskip("torch")
+    lam, mu = M.random_field(8, 8, 8, seed=2)
+    g = gfp.Grid(8, 8, 8)
+    g.set_phases(lam, mu)
+    sch = gfp.scheme("AFB_R", "PCD", "FP64")
+    g.solve(sch, [0.002, 0, 0, 0, 0, 0.001], 1e-10, 5000)
+    u_host = g.displacement(sch)
+    u_dev = torch.empty((3, 8, 8, 8), dtype=torch.float64, device="cuda")
+    g.displacement(sch, out=u_dev)
+    np.testing.assert_array_equal(u_dev.cpu().numpy(), u_host)
+    g.close()

@@ -108,3 +108,21 @@ def test_unsupported_with_eigenstrain(gfp):
     with pytest.raises(ValueError):
         g.set_eigenstrain(np.zeros((6, 8, 8, 7)))
     g.close()
+
+
+def test_eigenstrain_from_device_memory(gfp):
+    """The eigenstrain given as a CUDA tensor (device copy) gives the same solve as from host memory."""
+    torch = pytest.importorskip("torch")
+    lam, mu = M.random_field(8, 8, 8, seed=4)
+    es = _eigenstrain((8, 8, 8), 6)
+    E = [0.001, 0.0, -0.002, 0.0, 0.0, 0.003]
+    g = gfp.Grid(8, 8, 8)
+    g.set_phases(lam, mu)
+    g.set_eigenstrain(es)
+    r_host = g.solve(gfp.scheme("AFB_R", "PCD", "FP64"), E, 1e-11, 5000)
+    eps_host = g.strain()
+    g.set_eigenstrain(torch.from_numpy(es).cuda())
+    r_dev = g.solve(gfp.scheme("AFB_R", "PCD", "FP64"), E, 1e-11, 5000)
+    assert r_host.iters == r_dev.iters
+    np.testing.assert_array_equal(g.strain(), eps_host)
+    g.close()
