@@ -187,31 +187,46 @@ __global__ void dgo_table_kernel(double* __restrict__ tab, Dims d, const double*
     double S4[15];
     for (int q = 0; q < 15; ++q) S4[q] = 0.0;
     if (o1 != 0 || o2 != 0 || o3 != 0) {
+      // FP64 division is slow on this GPU: the axis scales are precomputed, each term takes one
+      // reciprocal of |k|^2, and the fourth moments are formed from the six pair products
+      const double f1 = two_pi / ((double)d.n1 * h), f2 = two_pi / ((double)d.n2 * h), f3 = two_pi / ((double)d.n3 * h);
       for (int v3 = -m3; v3 < m3; ++v3) {
         const double s3 = w3[o3 * 2 * m3 + (v3 + m3)];
         if (s3 == 0.0) continue;
-        const double k3 = two_pi * (double)((long long)v3 * d.n3 + o3) / ((double)d.n3 * h);
+        const double k3 = f3 * (double)((long long)v3 * d.n3 + o3);
         for (int v2 = -m2; v2 < m2; ++v2) {
           const double s2 = w2[o2 * 2 * m2 + (v2 + m2)];
           if (s2 == 0.0) continue;
-          const double k2 = two_pi * (double)((long long)v2 * d.n2 + o2) / ((double)d.n2 * h);
+          const double k2 = f2 * (double)((long long)v2 * d.n2 + o2);
           const double s23 = s2 * s3;
+          const double p22 = k2 * k2, p33 = k3 * k3, p23 = k2 * k3;
           for (int v1 = -m1; v1 < m1; ++v1) {
             const double s1 = w1[o1 * 2 * m1 + (v1 + m1)];
             if (s1 == 0.0) continue;
-            const double k1 = two_pi * (double)((long long)v1 * d.n1 + o1) / ((double)d.n1 * h);
-            const double kk = k1 * k1 + k2 * k2 + k3 * k3;
+            const double k1 = f1 * (double)((long long)v1 * d.n1 + o1);
+            const double p11 = k1 * k1;
+            const double kk = p11 + p22 + p33;
             if (kk == 0.0) continue;
-            const double w = s1 * s23;
-            const double a = w / kk, b = a / kk;
-            const double k[3] = {k1, k2, k3};
-            S2[0] += a * k1 * k1; S2[1] += a * k2 * k2; S2[2] += a * k3 * k3;
-            S2[3] += a * k2 * k3; S2[4] += a * k1 * k3; S2[5] += a * k1 * k2;
+            const double inv = 1.0 / kk;
+            const double a = s1 * s23 * inv, b = a * inv;
+            // pair products k_i k_j, i <= j: (11, 12, 13, 22, 23, 33)
+            const double pp[6] = {p11, k1 * k2, k1 * k3, p22, p23, p33};
+            S2[0] += a * p11; S2[1] += a * p22; S2[2] += a * p33;
+            S2[3] += a * p23; S2[4] += a * pp[2]; S2[5] += a * pp[1];
+            // S4 entries in the order i <= j <= p <= r: k_i k_j k_p k_r = (k_i k_j)(k_p k_r)
             int q = 0;
+#pragma unroll
             for (int i = 0; i < 3; ++i)
+#pragma unroll
               for (int j = i; j < 3; ++j)
+#pragma unroll
                 for (int p = j; p < 3; ++p)
-                  for (int r = p; r < 3; ++r, ++q) S4[q] += b * k[i] * k[j] * k[p] * k[r];
+#pragma unroll
+                  for (int r = p; r < 3; ++r, ++q) {
+                    const int ij = i == 0 ? j : (i == 1 ? 2 + j : 5);
+                    const int pr = p == 0 ? r : (p == 1 ? 2 + r : 5);
+                    S4[q] += b * pp[ij] * pp[pr];
+                  }
           }
         }
       }
