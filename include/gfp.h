@@ -84,6 +84,8 @@ typedef struct {
   int status;             /* gfp_status of the solve */
   double* residual_history; /* caller-owned host array of history_cap doubles, or NULL */
   int history_cap;
+  int launches;           /* GPU kernels this call launched (iterations are launched in chunks between
+                             convergence checks, so a few after convergence run as no-ops) */
 } gfp_result;
 
 /* Create a grid of n1 x n2 x n3 voxels with spacing h on `cuda_stream` (a cudaStream_t, NULL = legacy

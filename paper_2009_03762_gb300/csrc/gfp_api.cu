@@ -421,6 +421,7 @@ struct gfp_grid_s {
   bool estar_on = false;
   double E_last[6] = {0, 0, 0, 0, 0, 0};  // mean strain of the last solve (displacement output)
   bool have_solution = false;
+  long long launches = 0;            // kernels launched by the current gfp_solve call
 };
 
 
@@ -645,6 +646,7 @@ PolarParams fp64_xparams(gfp_grid g) {
 
 void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta) {
   const Dims& d = g->d;
+  g->launches += 5;
   const PolarParams pp = fp64_xparams(g);
   Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
                          have_delta ? PX_DELTA : 0, nullptr, nullptr, g->st, &pp);
@@ -670,6 +672,8 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   gp.c_lm = (g->lam_h + g->mu_h) / (g->mu_h * (g->lam_h + 2.0 * g->mu_h));
   gp.invN = 1.0 / (double)g->d.N;
   gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
+  gp.half_shift = 0;
+  gp.dgo = nullptr;
   SolveState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.maxit = maxit;
@@ -682,6 +686,7 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   if (!resume) {
     fill_eps_kernel<<<std::min<long long>(4096, (g->d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, g->d.N, E[0], E[1],
                                                                                             E[2], E[3], E[4], E[5]);
+    g->launches += 1;
   }
   *g->st_host = s0;
   GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
@@ -707,6 +712,7 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   if (out) {
     out->iters = s.it;
     out->outer = 0;
+    out->launches = (int)g->launches;
     out->residual = s.eta;
     for (int c = 0; c < 6; ++c) out->sigma_mean[c] = s.T0[c] / (double)g->d.N;
     out->status = status;
@@ -772,6 +778,7 @@ GammaParams<R> gamma_params(gfp_grid g, int op, const R* const* A, const R* cons
 // exact FP64 residual and mean stress, and v = T kt stored as the inner iterations' source.
 void residual_pass64(gfp_grid g, const GammaParams<double>& gp, bool with_corr) {
   const Dims& d = g->d;
+  g->launches += 4;
   const PolarParams pp = fp64_xparams(g);
   Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0,
                          with_corr ? g->eps32 : nullptr, g->cmean, g->st, &pp);
@@ -785,6 +792,7 @@ void residual_pass64(gfp_grid g, const GammaParams<double>& gp, bool with_corr) 
 // v = T kt + v64, Delta = -Gamma0(v) / N, inverse.
 void inner_iteration32(gfp_grid g, const GammaParams<float>& gp, int flags) {
   const Dims& d = g->d;
+  g->launches += 5;
   float2* spec32 = reinterpret_cast<float2*>(g->spec);
   Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, flags,
                         nullptr, nullptr, g->st_in);
@@ -811,11 +819,13 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->lam, g->lam32, d.N);
     to_float_kernel<<<cvb, 256, 0, g->stream>>>(g->mu, g->mu32, d.N);
     g->lam32_valid = true;
+    g->launches += 2;
   }
   const GammaParams<double> gp64 = gamma_params<double>(g, sc->op, g->tabA, g->tabB);
   const GammaParams<float> gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
   fill_eps_kernel<<<std::min<long long>(4096, (d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, d.N, E[0], E[1], E[2],
                                                                                        E[3], E[4], E[5]);
+  g->launches += 1;
   SolveState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.maxit = 1 << 30;
@@ -861,6 +871,7 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     if (g->st_in_host->done == DONE_TIMEOUT) { status = GFP_ERR_DEVICE_TIMEOUT; break; }
     corr_mean_partial_kernel<<<cvb, 256, 0, g->stream>>>(g->eps32, d.N, g->cpart, nullptr);
     corr_mean_final_kernel<<<1, 32, 0, g->stream>>>(g->cpart, cvb, d.N, g->cmean, nullptr);
+    g->launches += 2;
     // the next outer pass re-arms the FP64 state (it counts outer passes; never stops on maxit)
     g->st_host->done = 0;
     GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
@@ -871,6 +882,7 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
   if (out) {
     out->iters = inner_total;
     out->outer = outer;
+    out->launches = (int)g->launches;
     out->residual = s.eta;
     for (int c = 0; c < 6; ++c) out->sigma_mean[c] = s.T0[c] / (double)d.N;
     out->status = status;
@@ -940,6 +952,7 @@ int ensure_dgo(gfp_grid g, int dgo_m) {
   const long long npts = (long long)d.n1h * d.n2 * d.n3;
   dgo_table_kernel<<<(int)std::min<long long>(4096, (npts + 127) / 128), 128, 0, g->stream>>>(
       g->dgo, d, w[0], w[1], w[2], ms[0], ms[1], ms[2], g->h, g->lam_h, g->mu_h);
+  g->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   for (int r = 0; r < 3; ++r) cudaFree(w[r]);
@@ -976,6 +989,7 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   const double enorm = std::sqrt(en2) * std::sqrt((double)d.N);
   fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, d.N, E[0], E[1],
                                                                                           E[2], E[3], E[4], E[5]);
+  g->launches += 1;
   SolveState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.maxit = maxit;
@@ -993,6 +1007,7 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
       Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
                              PX_POLAR | (j > 0 ? PX_DELTA : 0), nullptr, nullptr, g->st, &pp);
       if (j > 0) reduce_dgo_kernel<<<1, 256, 0, g->stream>>>(g->xpart, np, enorm, g->st, g->hist, g->hist_cap);
+      g->launches += j > 0 ? 5 : 4;
       Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
       Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_DGO,
                              nullptr);
@@ -1009,6 +1024,7 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   // mean stress of the final strain
   const int sb = (int)std::min<long long>(1024, (d.N + 255) / 256);
   stress_sum_partial_kernel<<<sb, 256, 0, g->stream>>>(g->eps, g->lam, g->mu, d.N, g->scratch);
+  g->launches += 1;
   std::vector<double> part(6 * (size_t)sb);
   GFP_CU(cudaMemcpyAsync(part.data(), g->scratch, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, g->stream));
   GFP_CU(cudaStreamSynchronize(g->stream));
@@ -1020,6 +1036,7 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   if (out) {
     out->iters = s.it;
     out->outer = 0;
+    out->launches = (int)g->launches;
     out->residual = s.eta;
     for (int c = 0; c < 6; ++c) {
       double acc = 0.0;
@@ -1251,6 +1268,7 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   if (g->estar_on && sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
   for (int c = 0; c < 6; ++c) g->E_last[c] = E[c];
   g->have_solution = true;
+  g->launches = 0;
   if (sc->prec == GFP_MIXED) {
     g->resume_pending = false;
     return solve_mixed(g, sc, E, tol, maxit, out);
@@ -1579,6 +1597,8 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
   gp.c_lm = (lam_h + mu_h) / (mu_h * (lam_h + 2.0 * mu_h));
   gp.invN = 1.0 / (double)d.N;
   gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
+  gp.half_shift = 0;
+  gp.dgo = nullptr;
   FftPlan plan[3];
   for (int r = 0; r < 3; ++r) plan[r] = make_plan_fixed(ns[r]);
   // the shared scratch keeps the previous call's contents: clear the spectrum, reset the state
@@ -1617,6 +1637,7 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
   if (out) {
     out->iters = sh.it;
     out->outer = 0;
+    out->launches = 1 + 5 * launched;
     out->residual = sh.eta;
     for (int c = 0; c < 6; ++c) out->sigma_mean[c] = sh.T0[c] / (double)d.N;
     out->status = status;

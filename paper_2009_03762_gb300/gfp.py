@@ -28,7 +28,8 @@ class Scheme(ctypes.Structure):
 class _Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("residual", ctypes.c_double),
                 ("sigma_mean", ctypes.c_double * 6), ("status", ctypes.c_int),
-                ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int)]
+                ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
+                ("launches", ctypes.c_int)]
 
 
 class GfpError(RuntimeError):
@@ -122,6 +123,7 @@ class Result:
     def __init__(self, r, status, history):
         self.iters = r.iters
         self.outer = r.outer
+        self.launches = r.launches
         self.residual = r.residual
         self.sigma_mean = np.array(list(r.sigma_mean))
         self.status = status
