@@ -60,3 +60,39 @@ def test_product_package_does_not_import_the_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert not bad.search(src), fn
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of gfp_scheme and gfp_result have the header's size and field
+    offsets (compiled with the host C compiler)."""
+    import ctypes
+    import shutil
+    from paper_2009_03762_gb300 import gfp
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    res_fields = [f[0] for f in gfp._Result._fields_]
+    sch_fields = [f[0] for f in gfp.Scheme._fields_]
+    # same member names, in order, as the header's typedefs (a trailing int could hide in padding)
+    hdr = open(os.path.join(ROOT, "include", "gfp.h")).read()
+    for name, fields in (("gfp_result", res_fields), ("gfp_scheme", sch_fields)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*%s;" % name, hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        members = re.findall(r"(\w+)\s*(?:\[\d+\])?\s*;", body)
+        assert members == fields, (name, members, fields)
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gfp.h"', "int main(void) {",
+             '  printf("gfp_result %zu\\n", sizeof(gfp_result));', '  printf("gfp_scheme %zu\\n", sizeof(gfp_scheme));']
+    lines += ['  printf("r.%s %%zu\\n", offsetof(gfp_result, %s));' % (f, f) for f in res_fields]
+    lines += ['  printf("s.%s %%zu\\n", offsetof(gfp_scheme, %s));' % (f, f) for f in sch_fields]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
+    assert int(out["gfp_result"]) == ctypes.sizeof(gfp._Result)
+    assert int(out["gfp_scheme"]) == ctypes.sizeof(gfp.Scheme)
+    for f in res_fields:
+        assert int(out["r." + f]) == getattr(gfp._Result, f).offset, f
+    for f in sch_fields:
+        assert int(out["s." + f]) == getattr(gfp.Scheme, f).offset, f
