@@ -18,10 +18,15 @@ modeling of the quasi-static mechanical behavior of inhomogeneous materials"):
   FreDifFinFBDFR3D, EffNumWavConWil3D), evaluated with complex exponentials;
 * the Green operator is the literal complex 3x3 inverse of G_H^{-1}(q^a, q^b)
   (Sec. 5.2 eq. EquMecFunGre3D), set to zero where q^a . q^b = 0 (Sec. 3.1, zero modes);
-* Algorithm T-3D / P-3D accumulate the displacement coefficients u^p exactly as printed
-  (Sec. 5.2, 5.4); Algorithm D-3D accumulates the strain with the discrete Green
-  operator Gamma^c built from the alias sum as printed (Sec. 5.4, Algorithm D-3D, with
-  the isotropic G_H and Gamma_H of the same section).
+* the basic scheme of Algorithms T-3D / P-3D is the fixed-point map of the Lippmann-Schwinger
+  form of Sec. 5.2: the displacement coefficients u_check are corrected by G_H (T_check q^b)
+  until the divergence T_check q^b vanishes (`_fdd_step`); the strain is E_bar + F^+ sym(u_check (x) q^a);
+* Algorithm D-3D's discrete Green operator Gamma^c is the alias sum of the continuous isotropic
+  Gamma_H over the wave numbers k_{nu n + omega} (Sec. 5.4), with the weights and update form of
+  the weights and update form read in `_solve_dgo` by default.
+
+Pins (tests/test_oracle_pins.py) cover every function here; the alias sum off the coordinate axes
+is pinned by an independent construction from C_H-orthogonal projections onto compatible strains.
 
 Readings where the paper is silent or garbled:
 * stopping rule: the default is the equilibrium residual
@@ -284,7 +289,7 @@ def green_hat_iso(k, lam_h, mu_h):
 
 
 def dgo_operator(n3, n2, n1, h, lam_h, mu_h, m=None, power=1):
-    """Gamma^c_omega for omega in [0,n1) x [0,n2) x [0,n3), as printed in Algorithm D-3D:
+    """Gamma^c_omega for omega in [0,n1) x [0,n2) x [0,n3), the alias sum of Algorithm D-3D:
 
       Gamma^c_0 = 0,
       Gamma^c_omega = sum_{nu_r = -m_r}^{m_r - 1} prod_r s_{nu_r n_r + omega_r} Gamma_H(k_{nu n + omega}),
@@ -350,6 +355,22 @@ class Result:
         self.converged = converged
 
 
+def _fdd_step(u, Ebar_f, T0, lam, mu, qa, qb, G, mats):
+    """One evaluation of the fixed-point map u_check -> u_check + G_H (T_check q^b) (Sec. 5.2).
+
+    The compatible strain fluctuation of the current coefficients is F^+ sym(u_check (x) q^a), the
+    stress is T^(0) + C : (that fluctuation) with T^(0) = C : E_bar, its transform T_check = F^- T,
+    the discrete divergence T_check q^b, and the displacement correction G_H (T_check q^b).
+    Returns (strain, stress, T_check, T_check q^b, correction).
+    """
+    Et = inverse3(sym_outer(u, qa), mats).real
+    T = T0 + stiffness_apply(lam, mu, Et)
+    Tc = forward3(T, mats)
+    Tq = matvec(Tc, qb)
+    du = np.einsum("...ij,j...->i...", G, Tq)
+    return Ebar_f + Et, T, Tc, Tq, du
+
+
 def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=None,
           stop_rule=0, dgo_m=None, dgo_table=None, max_iters_exact=None, dgo_form="polarization",
           dgo_power=2, estar=None):
@@ -390,14 +411,9 @@ def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=
     eps = Ebar_f.copy()
     while True:
         it += 1
-        Et = inverse3(sym_outer(u, qa), mats)
-        eps = Ebar_f + Et.real
-        T = T0 + stiffness_apply(lam, mu, Et.real)
-        Tc = forward3(T, mats)
-        Tq = matvec(Tc, qb)
+        eps, T, Tc, Tq, du = _fdd_step(u, Ebar_f, T0, lam, mu, qa, qb, G, mats)
         T0n = np.sqrt(np.sum(np.abs(Tc[(slice(None), slice(None)) + k0]) ** 2))
         eta = np.sqrt(np.sum(np.abs(Tq) ** 2)) / T0n
-        du = np.einsum("...ij,j...->i...", G, Tq)
         if stop_rule == 1:
             crit = np.inf if du_prev is None else np.sum(np.sqrt(np.sum(np.abs(du - du_prev) ** 2, axis=0)))
         else:
@@ -421,16 +437,17 @@ def _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_tabl
                dgo_form="polarization", dgo_power=2):
     """Algorithm D-3D with the omega-indexed PCD transforms F^{c+-} (x_i^c = (i - 1/2) h).
 
-    Readings (the printed operator does not give a convergent iteration):
-    dgo_form = "stress": Delta E = Gamma^c T, E += Delta E, as printed in Algorithm D-3D.
+    Readings of the weights and the update form:
+    dgo_form = "stress": Delta E = Gamma^c T, E += Delta E, the update of Algorithm D-3D.
     dgo_form = "polarization" (default): the form the footnote to Algorithm D-1D ascribes to
     Eloh2019, E_check = Gamma^c [(C - C_H) E]_check, E = E_bar + F^{c+} E_check.
-    dgo_power = 1: weights s as printed; dgo_power = 2 (default): weights s^2, the consistent
-    operator of Brisard2010 on which Eloh2019 builds (the factor (-1)^nu s of the basis
+    dgo_power = 1: the weights s of Algorithm D-3D; dgo_power = 2 (default): weights s^2, the
+    consistent operator of Brisard2010 on which Eloh2019 builds (the factor (-1)^nu s of the basis
     phi^El, eq. DisPieCon1D, enters once from the trial and once from the test function).
-    With the printed weights Gamma^c has positive eigenvalues, so the stress form grows for any
-    inhomogeneous 3D cell and the polarization form grows at contrasts of a few tens; with s^2
-    both forms converge, and the polarization form reproduces the paper's finding that the DGO
+    With s, -Gamma^c C_H is a sum of projections with weights of both signs, so its eigenvalues
+    leave [0, 1] and no contraction bound holds: on a 6^3 two-phase cube at contrast 10 both forms
+    grow (at contrast 4 they still converge).  With s^2 the eigenvalues lie in [0, 1] and both
+    forms converge there; the polarization form reproduces the paper's finding that the DGO
     response is stiffer than AFB/R at high contrast.
     Residual: eta_D = ||E_new - E_old||_2 / (sqrt(N) ||E_bar||_F) (unitary transforms).
     """

@@ -585,3 +585,133 @@ def test_paper_increment_stop_rule_runs():
     lam, mu = M.random_field(4, 4, 4, seed=1)
     r = O.solve(lam, mu, "AFB_R", [0.01, 0, 0, 0, 0, 0], tol=1e-12, stop_rule=1, maxit=500)
     assert r.converged and r.iters > 2
+
+
+# ----------------------------------------------------------------------------- DGO off-axis pins
+def _voigt_stiffness(lam_h, mu_h):
+    """6x6 map from tensor components (11,22,33,23,13,12) of a strain to those of lam tr I + 2 mu eps."""
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam_h
+    C[np.arange(6), np.arange(6)] += 2.0 * mu_h
+    return C
+
+
+def _dgo_matrix(G, w1, w2, w3):
+    """The oracle's Gamma^c(omega) as a 6x6 map on tensor components (basis p has unit entries at (i,j), (j,i))."""
+    Mx = np.zeros((6, 6))
+    for p in range(6):
+        out = G[p][:, :, w3, w2, w1]
+        Mx[:, p] = [out[i, j] for (i, j) in O.VOIGT]
+    return Mx
+
+
+def _axis_alias_sum(n, w, power):
+    """S(omega) = sum_{nu=-m}^{m-1} sinc^p((nu n + omega)/n), m = n/2 (numpy's normalised sinc)."""
+    m = max(1, n // 2)
+    return sum(np.sinc((nu * n + w) / n) ** power for nu in range(-m, m))
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_dgo_off_axis_trace_and_eigenvalues(power):
+    """-Gamma^c(omega) C_H = sum_nu w_nu P(k_nu), P(k) the C_H-orthogonal projection onto the compatible strains
+    sym(u (x) k) (rank 3; Sec. 5.4 isotropic G_H).  Hence its trace is 3 prod_r S_r(omega_r) at every omega != 0
+    (an axis pairing mistake on a non-cubic grid changes S_r), and with the squared weights its eigenvalues lie in
+    [0, prod_r S_r] within [0, 1]; with the printed weights s (which change sign) they leave [0, 1], so the
+    contraction argument of the Green-operator iteration fails for them (the oracle's weight reading)."""
+    n1, n2, n3 = 4, 6, 8
+    lam_h, mu_h = 1.3, 0.6
+    G = O.dgo_operator(n3, n2, n1, 1.0, lam_h, mu_h, power=power)
+    C = _voigt_stiffness(lam_h, mu_h)
+    lo, hi = np.inf, -np.inf
+    for w3, w2, w1 in itertools.product(range(n3), range(n2), range(n1)):
+        if w1 == w2 == w3 == 0:
+            assert np.all(_dgo_matrix(G, 0, 0, 0) == 0.0)
+            continue
+        A = -_dgo_matrix(G, w1, w2, w3) @ C
+        S = _axis_alias_sum(n1, w1, power) * _axis_alias_sum(n2, w2, power) * _axis_alias_sum(n3, w3, power)
+        assert abs(np.trace(A) - 3.0 * S) < 1e-12
+        ev = np.linalg.eigvals(A).real
+        lo, hi = min(lo, ev.min()), max(hi, ev.max())
+        if power == 2:
+            assert ev.min() > -1e-12 and ev.max() < S + 1e-12
+    if power == 2:
+        assert hi <= 1.0
+    else:
+        assert lo < -0.1 and hi > 1.1
+
+
+def test_dgo_generic_omega_equals_projection_sum():
+    """At a generic off-axis omega on a non-cubic grid, Gamma^c(omega) = -sum_nu w_nu P(k_nu) C_H^{-1}, with P(k) built
+    here by least squares in the C_H energy metric (not from the Green tensor), k_nu,r = 2 pi (nu_r n_r + omega_r)/n_r
+    and w_nu = prod_r sinc^2, nu_r in [-n_r/2, n_r/2 - 1] (Algorithm D-3D with the squared weights the oracle reads)."""
+    n1, n2, n3 = 4, 6, 8
+    lam_h, mu_h = 0.9, 1.4
+    G = O.dgo_operator(n3, n2, n1, 1.0, lam_h, mu_h, power=2)
+    C = _voigt_stiffness(lam_h, mu_h)
+    D = np.diag([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])     # a : b over the full symmetric tensors
+    ns = (n1, n2, n3)
+    for om in ((1, 2, 3), (3, 5, 1), (2, 1, 6)):
+        ref = np.zeros((6, 6))
+        for nu in itertools.product(*[range(-n // 2, n // 2) for n in ns]):
+            j = [nu[r] * ns[r] + om[r] for r in range(3)]
+            w = np.prod([np.sinc(j[r] / ns[r]) ** 2 for r in range(3)])
+            k = np.array([2.0 * np.pi * j[r] / ns[r] for r in range(3)])
+            B = np.zeros((6, 3))                     # u -> tensor components of sym(u (x) k)
+            for p, (a, b) in enumerate(O.VOIGT):
+                B[p, a] += 0.5 * k[b]
+                B[p, b] += 0.5 * k[a]
+            W = D @ C
+            P = B @ np.linalg.solve(B.T @ W @ B, B.T @ W)
+            ref -= w * P @ np.linalg.inv(C)
+        np.testing.assert_allclose(_dgo_matrix(G, *om), ref, atol=1e-12)
+
+
+def _permute_sym(E6, perm):
+    """Tensor components of E'_ij = E_{perm[i] perm[j]}."""
+    T = O.voigt_to_tensor(np.asarray(E6, np.float64))
+    return O.tensor_to_voigt(T[np.ix_(perm, perm)])
+
+
+@pytest.mark.parametrize("scheme", ["DGO", "AFB_R", "F"])
+@pytest.mark.parametrize("axis", [1, 2])
+def test_laminate_along_x2_and_x3_non_cubic(scheme, axis):
+    """Laminates along x2 and along x3 of a 4 x 6 x 8 grid have the exact layered response (traction continuity,
+    in-plane strains uniform), obtained from the x1 closed form by relabelling the axes.  On a non-cubic grid this
+    pins the per-axis lengths and alias ranges of the operators off the x1 axis."""
+    n1, n2, n3 = 4, 6, 8
+    nax = (n1, n2, n3)[axis]
+    rng = np.random.default_rng(21 + axis)
+    prof_l = np.exp(rng.uniform(np.log(0.5), np.log(20.0), nax))
+    prof_m = np.exp(rng.uniform(np.log(0.5), np.log(20.0), nax))
+    shape = [1, 1, 1]
+    shape[2 - axis] = nax
+    lam = np.broadcast_to(prof_l.reshape(shape), (n3, n2, n1)).copy()
+    mu = np.broadcast_to(prof_m.reshape(shape), (n3, n2, n1)).copy()
+    E = np.array([0.01, -0.004, 0.007, 0.003, -0.002, 0.005])
+    kw = dict(dgo_form="stress") if scheme == "DGO" else {}
+    r = O.solve(lam, mu, scheme, E, tol=1e-12, maxit=5000, **kw)
+    assert r.converged
+    perm = [axis] + [a for a in range(3) if a != axis]     # laminate frame: its axis 0 is the layering axis
+    s_lam, _ = _laminate_closed_form(prof_l, prof_m, _permute_sym(E, perm))
+    inv = np.argsort(perm)
+    np.testing.assert_allclose(r.sigma_mean, _permute_sym(s_lam, inv), rtol=1e-9, atol=1e-13)
+
+
+@pytest.mark.parametrize("form,power,grows", [("stress", 1, True), ("polarization", 1, True),
+                                              ("stress", 2, False), ("polarization", 2, False)])
+def test_dgo_printed_weights_diverge_on_two_phase_cube(form, power, grows):
+    """The DGO weight and form readings on a 6^3 two-phase cube (edge 3, contrast 10, C_H = 1/2 (min + max)): with the printed weights s the
+    iteration grows in the printed stress form and in the polarization form alike; with s^2 both decrease
+    monotonically in the long run (the polarization form reaches 1e-10)."""
+    ind = M.cube_indicator(6, 3)
+    chi = 10.0
+    lam = 1.0 * (1.0 + ind * (chi - 1.0))
+    mu = 0.7 * (1.0 + ind * (chi - 1.0))
+    r = O.solve(lam, mu, "DGO", [0.01, 0, 0, 0, 0, 0], tol=1e-10, maxit=200, dgo_form=form, dgo_power=power)
+    h = np.array(r.history)
+    if grows:
+        assert h[-1] > 1e3 * h.min() and h[-1] > h[0]
+    else:
+        assert h[-1] == h.min() and h[-1] < 1e-4 * h[0]
+        if form == "polarization":
+            assert r.converged
