@@ -22,14 +22,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "voxel-iterations/s"
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture (profiles/), valid
-# only while the kernel sources hash to the value recorded with it; otherwise the traffic is unknown.
+# DRAM bytes (read + write) per launch of the dominant kernel from ncu captures, recorded in
+# profiles/ncu_traffic.json with the hash of the kernel sources they were taken on; a record counts only
+# while the sources still hash to that value, otherwise the traffic is unknown (null).
 KERNEL_SOURCES = ("gfp_fft.cuh", "gfp_fftc.cuh", "gfp_kernels.cuh", "gfp_kimpl.cuh")
-NCU_TRAFFIC = {
-    # pass_z_c2_kernel<float, 256>, 8-column z tiles, one FP32 inner iteration of the 256^3 workload
-    ("pass_z_gamma", 256, "MIXED", 8): {"bytes": 624.016896e6 + 369.470208e6,
-                                        "sources_sha1": "51e241bf9448dd86322e173c51d35360de4e1ef9"},
-}
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
 def kernel_sources_sha1():
@@ -44,10 +41,16 @@ def kernel_sources_sha1():
 def ncu_traffic(kernel, n, prec, tiles):
     """Recorded DRAM traffic per launch for this kernel and configuration, or None."""
     zc = abs(tiles[2]) if tiles else None
-    rec = NCU_TRAFFIC.get((kernel, n, prec, zc))
-    if rec is None or rec["sources_sha1"] != kernel_sources_sha1():
+    try:
+        with open(TRAFFIC_PATH) as f:
+            recs = json.load(f)["records"]
+    except (OSError, ValueError, KeyError):
         return None
-    return rec["bytes"]
+    sha = kernel_sources_sha1()
+    for rec in recs:
+        if (rec["kernel"], rec["n"], rec["prec"], rec["z_cols"]) == (kernel, n, prec, zc) and rec["sources_sha1"] == sha:
+            return rec["dram_read_bytes"] + rec["dram_write_bytes"]
+    return None
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 

@@ -203,11 +203,13 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
 /* Static message for a status code. */
 const char* gfp_error_string(int status);
 
-/* Fault injection for tests of failure detection (no counterpart in the paper).  kind 1: every later
- * TMA-fed z-pass makes its tile barrier expect `value` more bytes than its loads deliver, so the bounded
- * wait gives up (after about a second, then waits as long again for the loads already issued) and the
- * solve returns GFP_ERR_DEVICE_TIMEOUT with the CUDA context intact; value 0 turns it off.  No GPU fault
- * is involved.  Unknown kinds or values above 1 MiB return GFP_ERR_ARG.  Not thread-safe. */
+/* Fault injection for tests of failure detection (no counterpart in the paper).  kind 1, value 1: every
+ * later TMA-fed z-pass makes its first tile wait poll, with a short budget (2^22 cycles), a barrier that
+ * nothing arrives at, so the wait runs out as a real one would after about a second: the kernel marks
+ * the solve timed out, waits (bounded) until the tile loads it has issued have landed, and returns, and
+ * the solve returns GFP_ERR_DEVICE_TIMEOUT with the CUDA context intact.  Value 0 turns it off.  No GPU
+ * fault is involved and the tile barriers' byte counts stay those of the loads.  Other kinds or values
+ * return GFP_ERR_ARG.  Not thread-safe. */
 int gfp_set_fault_injection(int kind, int value);
 
 /* Detail of the last CUDA runtime failure seen by this thread (CUDA's message, code and source line),

@@ -72,7 +72,7 @@ __global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, S
   }
 }
 
-unsigned g_inject_tma_extra_tx = 0;
+unsigned g_inject_tma_timeout = 0;
 
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap) {
   reduce_eta_kernel<<<1, 1024, 0, s>>>(partials, np, st, hist, hist_cap);
@@ -1141,8 +1141,8 @@ extern "C" {
 const char* gfp_last_error_detail(void) { return g_detail; }
 
 int gfp_set_fault_injection(int kind, int value) {
-  if (kind != 1 || value < 0 || value > (1 << 20)) return GFP_ERR_ARG;
-  g_inject_tma_extra_tx = (unsigned)value;
+  if (kind != 1 || value < 0 || value > 1) return GFP_ERR_ARG;
+  g_inject_tma_timeout = (unsigned)value;
   return GFP_OK;
 }
 
@@ -1637,7 +1637,7 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
   if (out) {
     out->iters = sh.it;
     out->outer = 0;
-    out->launches = 1 + 5 * launched;
+    out->launches = 2 + 5 * launched;  // phase statistics and strain fill, then five kernels per iteration
     out->residual = sh.eta;
     for (int c = 0; c < 6; ++c) out->sigma_mean[c] = sh.T0[c] / (double)d.N;
     out->status = status;

@@ -587,8 +587,8 @@ struct Passes {
 
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap);
 
-// Test-only fault injection: extra bytes the TMA z-pass barrier waits for (0 = off).
-extern unsigned g_inject_tma_extra_tx;
+// Test-only fault injection: nonzero makes the TMA z-pass treat its first tile wait as timed out.
+extern unsigned g_inject_tma_timeout;
 
 template <typename R> bool cz_cols_ok(int n3, int cols);
 template <typename R> bool cz_tma_ok(int n3, int cols);

@@ -160,7 +160,7 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
         const int gsz = std::min(ntiles, tma_grid<R, N>(th, smt));                                            \
         pass_z_tma_kernel<R, N><<<gsz, th, smt, s>>>(*reinterpret_cast<const CUtensorMap*>(lc.ztmap), spec, tw, \
                                                       d, lc.z_cols, ntx, gp, partials, st, mode, vsrc,        \
-                                                      g_inject_tma_extra_tx);                                 \
+                                                      g_inject_tma_timeout);                                 \
         return;                                                                                               \
       }                                                                                                       \
       const size_t smc = sizeof(T) * (size_t)(2 * N + 7 * N * lc.z_cols) +                                   \

@@ -36,11 +36,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false after ~1 s (2^31 cycles) of polling.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+// Bounded wait: true when the phase completed, false after `budget` cycles of polling (default 2^31,
+// about a second).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  long long budget = (1LL << 31)) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
                                                             const typename C<R>::T* __restrict__ tw, Dims d, int cols,
                                                             int ntx, GammaParams<R> gp, double* __restrict__ partials,
                                                             SolveState* __restrict__ st, int mode,
-                                                            float2* __restrict__ vsrc, unsigned extra_tx) {
+                                                            float2* __restrict__ vsrc, unsigned inject_timeout) {
   typedef typename C<R>::T T;
   typedef CPlan<N> P;
   if (st->done) return;
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
   tiles[0] = reinterpret_cast<T*>(base);
   tiles[1] = tiles[0] + tile_elems;
   T* twl = tiles[1] + tile_elems;
-  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ __align__(8) unsigned long long bars[3];  // two tile buffers; [2] is never arrived at
   __shared__ double red[32];
   __shared__ int abort_flag;
   if ((smem_u32(tiles[0]) & 127u) != 0 || (smem_u32(tiles[1]) & 127u) != 0) {  // never issue a misaligned TMA
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
     mbar_fence_init();
     abort_flag = 0;
   }
@@ -96,8 +99,7 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
   const int w6 = 6 * cols;
   const int l = threadIdx.x % w6, t = threadIdx.x / w6;
   const int comp = l / cols, col = l % cols;
-  // extra_tx > 0 (fault injection in tests) makes the barrier expect bytes that never arrive
-  const unsigned tile_bytes = (unsigned)(tile_elems * sizeof(T)) + extra_tx;
+  const unsigned tile_bytes = (unsigned)(tile_elems * sizeof(T));
   constexpr int ZB = N < 256 ? N : 256;
   auto issue = [&](int tile, int b) {
     const int k2 = tile / ntx, k10 = (tile % ntx) * cols;
@@ -119,7 +121,12 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
       inflight_next = 1;
     }
     if (threadIdx.x == 0) {
-      if (!mbar_wait_bounded(&bars[b], (k >> 1) & 1)) abort_flag = 1;
+      // inject_timeout (tests of failure detection): wait instead, with a budget of 2^22 cycles, on
+      // bars[2], which nothing arrives at, so the wait runs out; the tile loads keep their true byte
+      // counts, so the drain below confirms that they have landed
+      const bool ok = inject_timeout ? mbar_wait_bounded(&bars[2], 0, 1LL << 22)
+                                     : mbar_wait_bounded(&bars[b], (k >> 1) & 1);
+      if (!ok) abort_flag = 1;
     }
     __syncthreads();
     if (abort_flag) {

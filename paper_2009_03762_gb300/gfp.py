@@ -333,9 +333,21 @@ def solve_noalloc(lam, mu, eps, sch, E, tol=1e-8, maxit=1000, h=1.0, ref=None, s
     for a in (lam, mu, eps):
         if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
             raise ValueError("expected contiguous CUDA float64 tensors")
+    if lam.dim() != 3 or tuple(mu.shape) != tuple(lam.shape) or tuple(eps.shape) != (6,) + tuple(lam.shape):
+        raise ValueError("expected lam, mu of shape (n3, n2, n1) and eps of shape (6, n3, n2, n1); got %s, %s, %s"
+                         % (tuple(lam.shape), tuple(mu.shape), tuple(eps.shape)))
+    if not (lam.device == mu.device == eps.device):
+        raise ValueError("lam, mu and eps must be on one device")
     n3, n2, n1 = lam.shape
+    with torch.cuda.device(lam.device):
+        return _solve_noalloc_call(lam, mu, eps, sch, E, tol, maxit, h, ref, stream, n1, n2, n3)
+
+
+def _solve_noalloc_call(lam, mu, eps, sch, E, tol, maxit, h, ref, stream, n1, n2, n3):
+    """The C call of solve_noalloc with the tensors' device current (the library looks up its scratch there)."""
+    import torch
     if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
+        stream = torch.cuda.current_stream(lam.device).cuda_stream
     Ec = (ctypes.c_double * 6)(*[float(v) for v in E])
     refp = None
     if ref is not None:

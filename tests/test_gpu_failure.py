@@ -18,7 +18,7 @@ def test_tma_wait_timeout_is_reported_and_context_survives():
     g.set_tiles(gfp.FP64, [0, 8, -4])           # TMA-fed z-pass, 4 columns
     sch = gfp.scheme("AFB_R")
     E = [0.01, 0, 0, 0, 0, 0]
-    assert L.gfp_set_fault_injection(1, 64) == 0
+    assert L.gfp_set_fault_injection(1, 1) == 0
     try:
         r = g.solve(sch, E, 1e-8, 3)
     except gfp.GfpError as e:
@@ -33,3 +33,4 @@ def test_tma_wait_timeout_is_reported_and_context_survives():
     assert r2.iters == 3
     assert np.linalg.norm(g.strain() - ref.eps) / np.linalg.norm(ref.eps) <= 1e-10
     assert L.gfp_set_fault_injection(7, 1) == -1
+    assert L.gfp_set_fault_injection(1, 64) == -1
