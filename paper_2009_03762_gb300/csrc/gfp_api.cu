@@ -500,7 +500,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tensor map of a half spectrum (FP32 or FP64 complex) as reals {2P, n2, n3, 6} with z-tiles of
-// `cols` columns x min(n3, 256) rows.  Returns false if the shape is not TMA-eligible.
+// `cols` columns x min(n3, 256) rows.  FP32 tiles of 8 columns (64-byte rows, the warp-shuffle z-pass)
+// use the 64-byte swizzle, all others none.  Returns false if the shape is not TMA-eligible.
 bool encode_ztmap(CUtensorMap* m, const void* spec, const Dims& d, int cols, int real_bytes) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc || cols < 1 || (2 * cols * real_bytes) % 16 != 0 || ((uintptr_t)spec & 15) != 0) return false;
@@ -511,7 +512,8 @@ bool encode_ztmap(CUtensorMap* m, const void* spec, const Dims& d, int cols, int
   cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = enc(m, real_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                          const_cast<void*>(spec), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         (real_bytes == 4 && cols == 8) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }

@@ -580,7 +580,7 @@ struct Passes {
                      const FftPlan& plan, const Dims& d, int flags, const float* corr, const double* corr_mean,
                      const SolveState* st, const PolarParams* pp = nullptr);
   static void pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spec, const T* tw, const FftPlan& plan,
-                     const Dims& d, const SolveState* st);
+                     const Dims& d, const SolveState* st, int comps = 6);
   static void pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw, const FftPlan& plan, const Dims& d,
                      const GammaParams<R>& gp, double* partials, SolveState* st, int mode, float2* vsrc);
 };

@@ -29,7 +29,9 @@ cudaError_t Passes<R>::setup() {
   GFP_FOR_CSIZES(GFP_SET)
 #undef GFP_SET
 #define GFP_SET_TMA(N) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_tma_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_tma_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if constexpr (sizeof(R) == 4 && SPlanOk<N>::ok)                                                     \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_z_s_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   GFP_FOR_CSIZES(GFP_SET_TMA)
 #undef GFP_SET_TMA
   return e;
@@ -121,8 +123,8 @@ void Passes<R>::pass_x(cudaStream_t s, const LaunchCfg& lc, T* spec, R* eps, con
 
 template <typename R>
 void Passes<R>::pass_y(cudaStream_t s, const LaunchCfg& lc, bool inverse, T* spec, const T* tw, const FftPlan& plan,
-                       const Dims& d, const SolveState* st) {
-  dim3 grid((d.n1h + lc.y_cols - 1) / lc.y_cols, d.n3, 6);
+                       const Dims& d, const SolveState* st, int comps) {
+  dim3 grid((d.n1h + lc.y_cols - 1) / lc.y_cols, d.n3, comps);
   switch (d.n2) {
 #define GFP_CASE(N)                                                                                 \
     case N: {                                                                                       \
@@ -154,6 +156,14 @@ void Passes<R>::pass_z(cudaStream_t s, const LaunchCfg& lc, T* spec, const T* tw
     case N: {                                                                                                 \
       const int th = 6 * lc.z_cols * CPlan<N>::T;                                                             \
       const size_t smt = sizeof(T) * (size_t)(N + 12 * N * lc.z_cols) + 128;                                 \
+      if constexpr (sizeof(R) == 4 && SPlanOk<N>::ok) {                                                       \
+        if (mode == PZ_INNER && lc.z_tma && lc.ztmap && lc.z_cols == 8 && !gp.nyq_avg) {                      \
+          pass_z_s_kernel<N><<<grid, 24 * CPlan<N>::T, zs_smem_bytes<N>(), s>>>(                              \
+              *reinterpret_cast<const CUtensorMap*>(lc.ztmap), reinterpret_cast<const float2*>(tw), d,        \
+              *reinterpret_cast<const GammaParams<float>*>(&gp), partials, st, vsrc);                         \
+          return;                                                                                             \
+        }                                                                                                     \
+      }                                                                                                       \
       if (mode != PZ_DGO && mode != PZ_DISP && lc.z_tma && lc.ztmap && (lc.z_cols * sizeof(T)) % 16 == 0 && th <= 384 &&        \
           smt <= 220 * 1024) {                    \
         const int ntiles = ntx * d.n2;                                                                        \
@@ -203,11 +213,12 @@ template <typename R> bool cz_cols_ok(int n3, int cols) {
     default: return cols <= 64;
   }
 }
-// Whether the TMA-fed z-pass can serve a tile of `cols` columns (its CTA has at most 384 threads).
+// Whether a TMA-fed z-pass can serve a tile of `cols` columns: the persistent kernel up to 384 threads,
+// and the 8-column warp-shuffle kernel for FP32 square plans.
 template <typename R> bool cz_tma_ok(int n3, int cols) {
   switch (n3) {
 #define GFP_CASE(N) \
-    case N: return cols >= 1 && 6 * cols * CPlan<N>::T <= 384;
+    case N: return (cols >= 1 && 6 * cols * CPlan<N>::T <= 384) || (cols == 8 && sizeof(R) == 4 && SPlanOk<N>::ok);
     GFP_FOR_CSIZES(GFP_CASE)
 #undef GFP_CASE
     default: return false;

@@ -5,6 +5,10 @@
 // buffers, signalling an mbarrier, while the CTA transforms, applies the Green operator to, and
 // inverse-transforms the previous tile.  Every wait on an mbarrier is bounded: after about a second it
 // marks the solve as timed out (SolveState::done = 4) and the CTA stops issuing work.
+//
+// The 8-column variant (pass_z_s_kernel, FP32 inner iterations, square plans N = T^2) loads its
+// whole tile with TMA in the 64-byte swizzle, transforms each line with T lanes of one warp that
+// exchange through __shfl_sync instead of shared memory, and stores the tile back with a TMA store.
 #pragma once
 #include <cuda.h>
 
@@ -235,6 +239,234 @@ __global__ void __launch_bounds__(384, ZBound<R, N>::blocks) pass_z_tma_kernel(c
     }
     fence_proxy_async();  // order this tile's generic shared accesses before the next async load into it
     __syncthreads();      // both the tile buffer and red[] are free for the next tile
+  }
+}
+
+
+// TMA store of a 4D box from shared memory (bulk group; the issuing thread waits for its reads).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map), "r"(c0),
+      "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Byte offset inside a 512-byte-aligned region as laid out by the 64-byte TMA swizzle
+// (CU_TENSOR_MAP_SWIZZLE_64B): the 16-byte chunk index (bits 4-5) is XORed with bits 7-8.
+__device__ __forceinline__ unsigned swz64(unsigned off) { return off ^ (((off >> 7) & 3u) << 4); }
+
+// a[j] <- a[(j - s) mod T] for a lane-dependent s in [0, T): one conditional move per bit of s.
+template <int T_, typename V>
+__device__ __forceinline__ void rot_right(V* a, int s) {
+#pragma unroll
+  for (int b = 1; b < T_; b <<= 1) {
+    const bool f = (s & b) != 0;
+    V tmp[T_];
+#pragma unroll
+    for (int j = 0; j < T_; ++j) tmp[j] = a[(j - b + T_) % T_];
+#pragma unroll
+    for (int j = 0; j < T_; ++j) a[j] = f ? tmp[j] : a[j];
+  }
+}
+
+// T x T transpose among the T consecutive lanes t of a group (T a power of two dividing 32): on entry
+// v[i] is the element this lane holds for lane i, on return v[s] is the element lane s held for this
+// lane.  The registers are rotated by the lane index before and after, so that in round j every lane
+// sends the same register j (to lane (t - j) mod T) and receives from lane (t + j) mod T.
+template <int T_, typename V>
+__device__ __forceinline__ void lane_transpose(V* v, int t) {
+  V u[T_];
+#pragma unroll
+  for (int j = 0; j < T_; ++j) u[j] = v[(T_ - j) % T_];
+  rot_right<T_>(u, t);  // u[j] = v[(t - j) mod T]
+#pragma unroll
+  for (int j = 1; j < T_; ++j) {
+    const int src = (t + j) & (T_ - 1);
+    V w;
+    w.x = __shfl_sync(0xffffffffu, u[j].x, src, T_);
+    w.y = __shfl_sync(0xffffffffu, u[j].y, src, T_);
+    u[j] = w;  // the element lane (t + j) mod T holds for this lane
+  }
+  rot_right<T_>(u, t);
+#pragma unroll
+  for (int j = 0; j < T_; ++j) v[j] = u[j];
+}
+
+// Line transform of length N = T^2 on the T lanes of a group (Stockham, two radix-T stages, the
+// exchange by lane_transpose).  On entry v[r] = x[t + T r]; on return v[k] = X[t + T k].
+template <int N, bool INV>
+__device__ __forceinline__ void sfft(float2* v, int t, const float2* __restrict__ tw) {
+  constexpr int T_ = CPlan<N>::T;
+  Dft<T_, INV, float2>::run(v);  // v[k] = y[T t + k], the element lane k needs for its stage-1 input t
+#pragma unroll
+  for (int k = 1; k < T_; ++k) {  // stage-1 twiddle w_N^{t k} of that element, applied by its sender
+    float2 w = tw[t * k];
+    if (INV) w.y = -w.y;
+    v[k] = cmul(v[k], w);
+  }
+  lane_transpose<T_>(v, t);        // v[s] = y[T s + t] (times its twiddle) = stage-1 input s
+  Dft<T_, INV, float2>::run(v);
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass_z_gamma with 8-column tiles, TMA in and out, warp-shuffle line transforms (FP32 inner iterations
+// of the mixed solve, PZ_INNER; square plans N = T^2 with N <= 256).  CTA = 8 k1 columns x 6 components
+// x all n3 rows at fixed k2, 24 T threads: thread (line, t) with line = threadIdx.x / T transforms
+// line A = (component line / 8, column line % 8) and line B (component + 3).  The tile is
+// [6][N rows][8 columns] of float2 in the 64-byte swizzle, so that the lane pattern of the transforms
+// (T rows of two adjacent columns per warp) and that of the Green step (4 rows x 8 columns per warp)
+// both touch each bank pair twice per warp access, the minimum for 256 bytes.  The Green step takes
+// all its FP64-residual sources from global memory in batches before its arithmetic.
+// ------------------------------------------------------------------------------------------------
+template <int N> struct SPlanOk {
+  static constexpr bool ok = CPlan<N>::ok && CPlan<N>::NST == 2 && CPlan<N>::R(0) == CPlan<N>::T &&
+                             CPlan<N>::R(1) == CPlan<N>::T && CPlan<N>::E == CPlan<N>::T && N <= 256;
+};
+template <int N> constexpr size_t zs_smem_bytes() { return (size_t)6 * N * 64 + 1024 + (size_t)2 * N * sizeof(float2); }
+
+template <int N>
+__global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                      const float2* __restrict__ tw, Dims d,
+                                                                      GammaParams<float> gp,
+                                                                      double* __restrict__ partials,
+                                                                      SolveState* __restrict__ st,
+                                                                      const float2* __restrict__ vsrc) {
+  constexpr int T_ = CPlan<N>::T, COLS = 8, NT = 24 * T_;
+  if (st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the swizzle pattern repeats every 512 bytes and TMA destinations with it must be so aligned:
+  // align the tile to 1024 bytes by hand (the launch adds 1024 bytes for this)
+  unsigned char* tile = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float2* twl = reinterpret_cast<float2*>(tile + 6 * N * 64);
+  float2* ab3 = twl + N;
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ double red[32];
+  __shared__ int abort_flag;
+  const int k10 = blockIdx.x * COLS, k2 = blockIdx.y;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, 6u * N * 64u);
+    for (int c = 0; c < 6; ++c) tma_load_4d(tile + c * N * 64, &tmap, &bar, 2 * k10, k2, 0, c);
+  }
+  for (int i = threadIdx.x; i < N; i += NT) {
+    twl[i] = tw[i];
+    float2 ab;
+    ab.x = gp.A[2][i];
+    ab.y = gp.B[2][i];
+    ab3[i] = ab;
+  }
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0)) abort_flag = 1;
+  __syncthreads();
+  if (abort_flag) {
+    if (threadIdx.x == 0) {
+      atomicExch(&st->done, (int)DONE_TIMEOUT);
+      mbar_wait_bounded(&bar, 0);  // the loads land in this CTA's shared memory: wait (bounded) for them
+    }
+    return;
+  }
+  const int t = threadIdx.x & (T_ - 1), line = threadIdx.x / T_;
+  const int col = line % COLS, compA = line / COLS;
+  auto el = [&](int c, int z, int cc) -> float2& {
+    return *reinterpret_cast<float2*>(tile + swz64((unsigned)(c * N * 64 + z * 64 + cc * 8)));
+  };
+  // forward transforms of lines A and B, in place (each thread owns rows t + T r of its lines)
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int c = compA + 3 * h;
+    float2 v[T_];
+#pragma unroll
+    for (int r = 0; r < T_; ++r) v[r] = el(c, t + T_ * r, col);
+    sfft<N, false>(v, t, twl);
+#pragma unroll
+    for (int k = 0; k < T_; ++k) el(c, t + T_ * k, col) = v[k];
+  }
+  __syncthreads();
+  // Green step: point p = threadIdx.x + NT q is (row p / 8, column p % 8)
+  float acc = 0.f;
+  {
+    const int cc = threadIdx.x & 7;
+    const int k1 = k10 + cc;
+    const bool live = k1 < d.n1h;
+    const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
+    (void)ny2;
+    const float b2 = gp.B[1][k2], a2 = gp.A[1][k2];
+    const float a1 = live ? gp.A[0][k1] : 0.f, b1 = live ? gp.B[0][k1] : 0.f;
+    const bool self1 = (k1 == 0) || (((d.n1 & 1) == 0) && (2 * k1 == d.n1));
+    constexpr int NQ = (N * COLS + NT - 1) / NT;
+    constexpr int GB = NQ < 3 ? NQ : 3;
+    float2 src[GB][3];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int z = (threadIdx.x + NT * q) >> 3;
+      if (q % GB == 0) {
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+          const int zu = (threadIdx.x + NT * (q + u)) >> 3;
+          if (q + u < NQ && zu < N && live) {
+            const long long vi = d.row(zu, k2) * d.P + k1;
+            src[u][0] = vsrc[vi];
+            src[u][1] = vsrc[d.S + vi];
+            src[u][2] = vsrc[2 * d.S + vi];
+          }
+        }
+      }
+      if (z >= N) continue;
+      float2 o[6];
+      if (live) {
+        float2 tt[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tt[c] = el(c, z, cc);
+        const float2 ab = ab3[z];
+        const float kt1 = a1 * b2 * ab.y, kt2 = a2 * ab.y * b1, kt3 = ab.x * b1 * b2;
+        float2 v1, v2, v3;
+        tk_vec<float>(tt, kt1, kt2, kt3, v1, v2, v3);
+        const float2* s3 = src[q % GB];
+        v1.x += s3[0].x; v1.y += s3[0].y; v2.x += s3[1].x; v2.y += s3[1].y; v3.x += s3[2].x; v3.y += s3[2].y;
+        float r2 = vnorm2(v1, v2, v3);
+        acc += self1 ? r2 : 2.f * r2;
+        gamma0_from_v<float>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { o[c].x = 0.f; o[c].y = 0.f; }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) el(c, z, cc) = o[c];
+    }
+  }
+  double accd = (double)acc;
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double sm = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) sm += __shfl_down_sync(0xffffffffu, sm, off);
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sm;
+  }
+  // inverse transforms, in place
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int c = compA + 3 * h;
+    float2 v[T_];
+#pragma unroll
+    for (int r = 0; r < T_; ++r) v[r] = el(c, t + T_ * r, col);
+    sfft<N, true>(v, t, twl);
+#pragma unroll
+    for (int k = 0; k < T_; ++k) el(c, t + T_ * k, col) = v[k];
+  }
+  // the tile back to global memory: make the generic-proxy writes visible to the TMA unit first
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 6; ++c) tma_store_4d(&tmap, tile + c * N * 64, 2 * k10, k2, 0, c);
+    bulk_commit_and_wait_read();
   }
 }
 

@@ -23,7 +23,8 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
 
 
-def test_laminate_256_along_x3_closed_form(gfp):
+@pytest.mark.parametrize("tiles", [BENCH_TILES, [2, 16, -8]])
+def test_laminate_256_along_x3_closed_form(gfp, tiles):
     """Layers stacked along x3 (the z-pass couples them): the normal stress s33 and the shears s13,
     s23 are uniform, so s33 = (E33 + <l/M>(E11 + E22)) / <1/M>, M = l + 2 mu, and
     s13 = E13 / <1/(2 mu)> (tensor components, no factor 2)."""
@@ -37,7 +38,7 @@ def test_laminate_256_along_x3_closed_form(gfp):
     E = np.array([0.004, -0.002, 0.01, 0.003, -0.002, 0.001])
     g = gfp.Grid(n, n, n)
     g.set_phases(lam, mu)
-    g.set_tiles(gfp.MIXED, BENCH_TILES)
+    g.set_tiles(gfp.MIXED, tiles)
     r = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), E, 1e-10, 20000)
     assert r.converged
     Mm = l3 + 2 * m3

@@ -60,10 +60,11 @@ def test_mixed_unsupported_combinations(gfp):
         assert e.value.code == -8
 
 
-@pytest.mark.parametrize("zcols", [8, 4, 2])
+@pytest.mark.parametrize("zcols", [8, -8, 4, 2])
 def test_mixed_z_tile_widths_on_256_columns(gfp, zcols):
-    """z-pass tiles of 8 columns (768-thread CTA), 4 and 2 on n3 = 256 with a ragged k1 range
-    (n1/2 + 1 = 9 columns): the mixed solve matches the FP64 GPU solve."""
+    """z-pass tiles of 8 columns (two lines per thread; -8: TMA-fed with warp-shuffle transforms), 4 and
+    2 on n3 = 256 with a ragged k1 range (n1/2 + 1 = 9 columns): the mixed solve matches the FP64 GPU
+    solve."""
     lam, mu = M.random_field(16, 8, 256, seed=5)
     E = [0.0, 0.0, 0.0, 0.3, 0.0, 0.0]
     g = gfp.Grid(16, 8, 256)
@@ -76,3 +77,21 @@ def test_mixed_z_tile_widths_on_256_columns(gfp, zcols):
     assert r64.converged
     assert _rel(eps, g.strain()) <= 1e-6
     assert _rel(r.sigma_mean, r64.sigma_mean) <= 1e-6
+
+
+def test_mixed_shuffle_z_pass_matches_oracle(gfp):
+    """The TMA-fed 8-column z-pass with warp-shuffle line transforms (square plan 64 = 8 x 8; the
+    256 = 16 x 16 plan is checked against the FP64 GPU solve above) against the FP64 oracle, with a
+    ragged k1 range (13 columns: a full and a partial tile)."""
+    shape = (24, 16, 64)
+    n1, n2, n3 = shape
+    lam, mu = M.random_spheres(shape, vf=0.25, rmin=2.0, rmax=4.0, contrast=20.0, seed=n3)
+    E = [0.002, 0.0, -0.001, 0.0, 0.004, 0.0]
+    g = gfp.Grid(n1, n2, n3)
+    g.set_phases(lam, mu)
+    g.set_tiles(gfp.MIXED, [2, 4, -8])
+    r = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), E, 1e-8, 20000)
+    assert r.converged and r.residual < 1e-8
+    ref = O.solve(lam, mu, "AFB_R", E, tol=1e-8, maxit=20000, disc="PCD")
+    assert _rel(r.sigma_mean, ref.sigma_mean) <= 1e-6
+    assert _rel(g.strain(), ref.eps) <= 1e-6
