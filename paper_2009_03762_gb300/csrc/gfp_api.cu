@@ -14,6 +14,7 @@
 
 #include "../../include/gfp.h"
 #include "gfp_kernels.cuh"
+#include "gfp_outer.cuh"
 
 using namespace gfp;
 
@@ -413,6 +414,8 @@ struct gfp_grid_s {
   bool mixed_ready = false;
   bool lam32_valid = false;
   CUtensorMap zmap64, zmap32;  // TMA descriptors of the z-tiles for lc64 / lc32
+  double* rpart = nullptr;     // per-CTA sums of the real-space FP64 outer pass, 8 per CTA
+  float2* ph32[3] = {nullptr, nullptr, nullptr};  // e^{i th_r / 2} per axis (stencil phase of AHC, AFB/R)
   // discrete Green operator table and the key it was built for
   double* dgo = nullptr;
   double dgo_key[4] = {0, 0, 0, 0};  // lambda_H, mu_H, m, valid
@@ -586,6 +589,10 @@ int global_setup() {
   std::call_once(g_setup_once, [] {
     g_setup_err = Passes<double>::setup();
     if (g_setup_err == cudaSuccess) g_setup_err = Passes<float>::setup();
+    if (g_setup_err == cudaSuccess)
+      g_setup_err = cudaFuncSetAttribute(rx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (g_setup_err == cudaSuccess)
+      g_setup_err = cudaFuncSetAttribute(rz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   if (g_setup_err != cudaSuccess) note_error(g_setup_err, __LINE__);
   return cuda_status(g_setup_err);
@@ -599,7 +606,8 @@ void free_grid(gfp_grid g) {
   cudaFree(g->eps_save);
   cudaFree(g->lam32); cudaFree(g->mu32); cudaFree(g->eps32); cudaFree(g->vsrc);
   for (int r = 0; r < 3; ++r) { cudaFree(g->tw32[r]); cudaFree(g->tabA32[r]); cudaFree(g->tabB32[r]); }
-  cudaFree(g->st_in); cudaFree(g->cmean); cudaFree(g->cpart);
+  cudaFree(g->st_in); cudaFree(g->cmean); cudaFree(g->cpart); cudaFree(g->rpart);
+  for (int r = 0; r < 3; ++r) cudaFree(g->ph32[r]);
   cudaFree(g->dgo); cudaFree(g->xpart); cudaFree(g->estar);
   if (g->st_host) cudaFreeHost(g->st_host);
   if (g->st_in_host) cudaFreeHost(g->st_in_host);
@@ -727,6 +735,27 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   return status;
 }
 
+// Real-space outer pass: stencil family of a scheme, CTA grid and count, z-transform tile width.
+int res_stencil(int op) { return op == OP_CD ? RS_CD : (op == OP_ACD ? RS_ACD : RS_AFD); }
+dim3 res64_grid(const Dims& d) {
+  return dim3((d.n1 + kResTX - 1) / kResTX, (d.n2 + kResTY - 1) / kResTY, (d.n3 + kResTZ - 1) / kResTZ);
+}
+int res64_blocks(const Dims& d) {
+  const dim3 g = res64_grid(d);
+  return (int)(g.x * g.y * g.z);
+}
+int rz_cols(int n3) {
+  int c = 16;
+  while (c > 1 && sizeof(float2) * 2 * (size_t)c * (n3 + 1) > 200 * 1024) c /= 2;
+  return c;
+}
+// th = 2 pi kappa / n for storage index j (kappa = j below the middle, j - n from it on: the Nyquist
+// index of an even axis is kappa = -n/2), as in the wave-vector tables
+double stencil_angle(int n, int j) {
+  const long long kap = (j < (n + 1) / 2) ? j : (long long)j - n;
+  return 2.0 * 3.14159265358979323846 * (double)kap / (double)n;
+}
+
 int ensure_mixed(gfp_grid g) {
   if (g->mixed_ready) return GFP_OK;
   const Dims& d = g->d;
@@ -751,6 +780,17 @@ int ensure_mixed(gfp_grid g) {
   GFP_CU(cudaMallocHost((void**)&g->st_in_host, sizeof(SolveState)));
   GFP_CU(cudaMalloc(&g->cmean, sizeof(double) * 6));
   GFP_CU(cudaMalloc(&g->cpart, sizeof(double) * 6 * 1024));
+  GFP_CU(cudaMalloc(&g->rpart, sizeof(double) * 8 * (size_t)res64_blocks(d)));
+  for (int r = 0; r < 3; ++r) {
+    std::vector<float2> ph(ns[r]);
+    for (int j = 0; j < ns[r]; ++j) {
+      const double th = stencil_angle(ns[r], j);
+      ph[j].x = (float)std::cos(0.5 * th);
+      ph[j].y = (float)std::sin(0.5 * th);
+    }
+    GFP_CU(cudaMalloc(&g->ph32[r], sizeof(float2) * ns[r]));
+    GFP_CU(cudaMemcpy(g->ph32[r], ph.data(), sizeof(float2) * ns[r], cudaMemcpyHostToDevice));
+  }
   const int pz32 = g->lc32.z_blocks;
   if (pz32 > g->np_max) {
     cudaFree(g->partials);
@@ -776,18 +816,58 @@ GammaParams<R> gamma_params(gfp_grid g, int op, const R* const* A, const R* cons
   return gp;
 }
 
-// FP64 outer pass: eps64 += corr - mean(corr) (if corr), sigma64 = C : eps64, forward 3D transform,
-// exact FP64 residual and mean stress, and v = T kt stored as the inner iterations' source.
-void residual_pass64(gfp_grid g, const GammaParams<double>& gp, bool with_corr) {
-  const Dims& d = g->d;
-  g->launches += 4;
-  const PolarParams pp = fp64_xparams(g);
-  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0,
-                         with_corr ? g->eps32 : nullptr, g->cmean, g->st, &pp);
-  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
-  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_RESIDUAL,
-                         g->vsrc);
-  launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
+// Real-space FP64 outer pass (gfp_outer.cuh) on explicit buffers, for single and batched solves:
+// eps += corr - mean(corr) (if corr), r = D^b C : (eps - estar), the FP64 residual and mean stress
+// into st (reduce_eta decides convergence).  r (FP32 [3][N]) goes to rbuf.  Every kernel is a no-op
+// while st is done (held batch slots).
+void outer_pass64(cudaStream_t s, const Dims& d, double h, int op, double* eps, const double* lam, const double* mu,
+                  const double* estar, const float* corr, const double* cmean, float* rbuf, double* rpart,
+                  double* partials, SolveState* st, long long& launches) {
+  if (corr) {
+    const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+    apply_corr64_kernel<<<cvb, 256, 0, s>>>(eps, corr, cmean, d.N, st);
+    ++launches;
+  }
+  const dim3 grid = res64_grid(d);
+  const double inv_h = 1.0 / h;
+  switch (res_stencil(op)) {
+    case RS_CD: residual64_kernel<RS_CD><<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
+    case RS_ACD: residual64_kernel<RS_ACD><<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
+    default: residual64_kernel<RS_AFD><<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
+  }
+  res64_sum_kernel<<<1, 256, 0, s>>>(rpart, res64_blocks(d), d.N, st, partials);
+  launch_reduce_eta(s, partials, 1, st, nullptr, 0);
+  launches += 3;
+}
+
+// The inner iterations' source v = T_check kt from the residual field r: FP32 transforms along x1
+// (rx_kernel), x2 (the y-pass on three components) and x3 with the stencil phase (rz_kernel).
+void outer_source32(cudaStream_t s, const LaunchCfg& lc32, const Dims& d, int op, const float* rbuf, float2* vsrc,
+                    float2* const* tw32, const FftPlan* plan, float2* const* ph, const SolveState* st,
+                    long long& launches) {
+  const long long nlines = (long long)d.n2 * d.n3;
+  const int L = 4;
+  const size_t smx = sizeof(float2) * 2 * (3 * L / 2) * (size_t)d.n1;
+  rx_kernel<<<(unsigned)((nlines + L - 1) / L), 256, smx, s>>>(rbuf, vsrc, tw32[0], plan[0], d, L, st);
+  Passes<float>::pass_y(s, lc32, false, vsrc, tw32[1], plan[1], d, st, 3);
+  const int zc = rz_cols(d.n3);
+  const size_t smz = sizeof(float2) * 2 * (size_t)zc * (d.n3 + 1);
+  const bool phase = res_stencil(op) == RS_AFD;
+  rz_kernel<<<dim3((d.n1h + zc - 1) / zc, d.n2, 3), 256, smz, s>>>(vsrc, tw32[2], plan[2], d, zc,
+                                                                   phase ? ph[0] : nullptr, phase ? ph[1] : nullptr,
+                                                                   phase ? ph[2] : nullptr, st);
+  launches += 3;
+}
+
+void residual_pass64(gfp_grid g, int op, bool with_corr) {
+  outer_pass64(g->stream, g->d, g->h, op, g->eps, g->lam, g->mu, g->estar_on ? g->estar : nullptr,
+               with_corr ? g->eps32 : nullptr, g->cmean, reinterpret_cast<float*>(g->spec), g->rpart, g->partials,
+               g->st, g->launches);
+}
+
+void inner_source32(gfp_grid g, int op) {
+  outer_source32(g->stream, g->lc32, g->d, op, reinterpret_cast<const float*>(g->spec), g->vsrc, g->tw32, g->plan,
+                 g->ph32, g->st, g->launches);
 }
 
 // One FP32 inner iteration on the correction: delta += d_delta, sigma = C32 : delta, forward,
@@ -823,7 +903,6 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     g->lam32_valid = true;
     g->launches += 2;
   }
-  const GammaParams<double> gp64 = gamma_params<double>(g, sc->op, g->tabA, g->tabB);
   const GammaParams<float> gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
   fill_eps_kernel<<<std::min<long long>(4096, (d.N + 255) / 256), 256, 0, g->stream>>>(g->eps, d.N, E[0], E[1], E[2],
                                                                                        E[3], E[4], E[5]);
@@ -840,7 +919,7 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
   bool with_corr = false;
   int status = GFP_ERR_NOT_CONVERGED;
   while (true) {
-    residual_pass64(g, gp64, with_corr);
+    residual_pass64(g, sc->op, with_corr);
     ++outer;
     GFP_CU(cudaGetLastError());
     GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
@@ -850,7 +929,8 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
     if (so.done == 3) { status = GFP_ERR_DIVERGED; break; }
     if (so.done == DONE_TIMEOUT) { status = GFP_ERR_DEVICE_TIMEOUT; break; }
     if (inner_total >= maxit) { status = GFP_ERR_NOT_CONVERGED; break; }
-    // inner solve of the correction equation from a zero correction
+    // inner solve of the correction equation from a zero correction, with the source of this residual
+    inner_source32(g, sc->op);
     SolveState si = s0;
     si.maxit = maxit - inner_total;
     si.tol = std::max(0.5 * tol, kInnerReduction * so.eta);
@@ -1446,7 +1526,8 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
       g->lam32_valid = true;
     }
     gp32 = gamma_params<float>(g, sc->op, g->tabA32, g->tabB32);
-    residual_pass64(g, gp, false);  // fills the inner source and T(0)
+    residual_pass64(g, sc->op, false);  // the FP64 residual, T(0) and the inner source
+    inner_source32(g, sc->op);
     GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
     GFP_CU(cudaStreamSynchronize(g->stream));
     SolveState si = s0;
@@ -1814,26 +1895,27 @@ struct BatchSlot {
   cudaStream_t stream = nullptr;
   LaunchCfg lc64, lc32;
   CUtensorMap zm64, zm32;
+  double* rpart = nullptr;  // per-CTA sums of the real-space outer pass
 };
 
 void free_slot(BatchSlot& s) {
   cudaFree(s.eps); cudaFree(s.eps32); cudaFree(s.spec); cudaFree(s.vsrc); cudaFree(s.partials);
-  cudaFree(s.st); cudaFree(s.st_in); cudaFree(s.cmean); cudaFree(s.cpart); cudaFree(s.acc);
+  cudaFree(s.st); cudaFree(s.st_in); cudaFree(s.cmean); cudaFree(s.cpart); cudaFree(s.acc); cudaFree(s.rpart);
   if (s.stream) cudaStreamDestroy(s.stream);
 }
 
-void slot_window(BatchSlot& s, const GammaParams<double>& gp64, const GammaParams<float>& gp32, double tol,
-                 int window) {
+void slot_window(BatchSlot& s, int op, const GammaParams<float>& gp32, double tol, int window) {
   gfp_grid g = s.g;
   const Dims& d = g->d;
   cudaStream_t st = s.stream;
   const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
   batch_gate_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, window);
-  Passes<double>::pass_x(st, s.lc64, s.spec, s.eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, 0, s.eps32, s.cmean,
-                         s.st);
-  Passes<double>::pass_y(st, s.lc64, false, s.spec, g->tw64[1], g->plan[1], d, s.st);
-  Passes<double>::pass_z(st, s.lc64, s.spec, g->tw64[2], g->plan[2], d, gp64, s.partials, s.st, PZ_RESIDUAL, s.vsrc);
-  launch_reduce_eta(st, s.partials, s.lc64.z_blocks, s.st, nullptr, 0);
+  // the FP64 outer pass and the inner source: no-ops while the slot's outer state is held or done
+  long long launches = 0;
+  outer_pass64(st, d, g->h, op, s.eps, g->lam, g->mu, nullptr, s.eps32, s.cmean, reinterpret_cast<float*>(s.spec),
+               s.rpart, s.partials, s.st, launches);
+  outer_source32(st, s.lc32, d, op, reinterpret_cast<const float*>(s.spec), s.vsrc, g->tw32, g->plan, g->ph32, s.st,
+                 launches);
   batch_arm_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, s.acc, tol, kInnerReduction, window);
   float2* spec32 = reinterpret_cast<float2*>(s.spec);
   for (int k = 0; k < window; ++k) {
@@ -1900,6 +1982,7 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
       A((void**)&s.cmean, sizeof(double) * 6);
       A((void**)&s.cpart, sizeof(double) * 6 * 1024);
       A((void**)&s.acc, sizeof(BatchAcc));
+      A((void**)&s.rpart, sizeof(double) * 8 * (size_t)res64_blocks(d));
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
       if (e != cudaSuccess) break;
       s.lc64 = g->lc64;
@@ -1958,9 +2041,8 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
     for (int i : active) {
       BatchSlot& s = slots[i];
       cudaStreamWaitEvent(s.stream, fork, 0);
-      const GammaParams<double> gp64 = gamma_params<double>(s.g, sc->op, s.g->tabA, s.g->tabB);
       const GammaParams<float> gp32 = gamma_params<float>(s.g, sc->op, s.g->tabA32, s.g->tabB32);
-      slot_window(s, gp64, gp32, tol, window);
+      slot_window(s, sc->op, gp32, tol, window);
       cudaEventRecord(joins[i], s.stream);
       cudaStreamWaitEvent(main, joins[i], 0);
     }
