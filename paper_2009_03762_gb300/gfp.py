@@ -322,6 +322,75 @@ def solve_batch(grids, sch, tol=1e-8, maxit=5000):
     return C.reshape(count, 6, 6), its, rc
 
 
+def batch_shard(costs, rank, world):
+    """Cells of a batch that rank `rank` of `world` solves.  Cells are dealt in order of decreasing cost
+    (e.g. voxel count) to the rank with the least total so far, ties to the lower rank: deterministic,
+    disjoint, covering, and balanced within one cell's cost."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += float(costs[i])
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def gather_batch(C_local, iters_local, idx_local, count, group=None):
+    """All-gather of every rank's batch results (torch.distributed, any backend) into C_eff [count, 6, 6]
+    and inner iterations [count, 6] on every rank."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    payload = ([int(i) for i in idx_local], np.asarray(C_local, dtype=np.float64).reshape(-1, 6, 6),
+               np.asarray(iters_local, dtype=np.int64).reshape(-1, 6))
+    objs = [None] * world
+    dist.all_gather_object(objs, payload, group=group)
+    C = np.full((count, 6, 6), np.nan)
+    its = np.full((count, 6), -1, dtype=np.int64)
+    for idx, Cl, il in objs:
+        if len(idx):
+            C[idx] = Cl
+            its[idx] = il
+    return C, its
+
+
+def _solve_cells(cells, sch, tol, maxit):
+    """gfp_solve_batch over (lam, mu) cells on this process's GPU; returns (C_eff, iterations, status)."""
+    import torch
+    grids = []
+    try:
+        for lam, mu in cells:
+            n3, n2, n1 = np.shape(lam)
+            g = Grid(n1, n2, n3, 1.0, torch.cuda.current_stream().cuda_stream)
+            g.set_phases(lam, mu)
+            grids.append(g)
+        if not grids:
+            return np.zeros((0, 6, 6)), np.zeros((0, 6), dtype=np.int32), 0
+        return solve_batch(grids, sch, tol, maxit)
+    finally:
+        for g in grids:
+            g.close()
+
+
+def solve_batch_sharded(make_cell, costs, sch, tol=1e-8, maxit=5000, group=None, solver=None):
+    """Batched homogenization across the ranks of torch.distributed (one GPU per rank): rank r builds the
+    cells batch_shard(costs, r, world) with make_cell(i) -> (lam, mu), solves them with gfp_solve_batch,
+    and every rank receives the full C_eff [count, 6, 6] and iterations [count, 6].  The only exchange is
+    the gather of the results; there is no collective on the data path.  `solver` replaces the local
+    solve (same signature as _solve_cells), e.g. in tests without a GPU.  Returns (C, iters, status)
+    with the worst local status over the ranks."""
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    idx = batch_shard(costs, rank, world)
+    C_l, it_l, rc = (solver or _solve_cells)([make_cell(i) for i in idx], sch, tol, maxit)
+    C, its = gather_batch(C_l, it_l, idx, len(costs), group)
+    codes = [None] * world
+    dist.all_gather_object(codes, int(rc), group=group)
+    worst = min(codes) if min(codes) < 0 else 0
+    return C, its, worst
+
+
 def solve_noalloc(lam, mu, eps, sch, E, tol=1e-8, maxit=1000, h=1.0, ref=None, stream=None):
     """Allocation-free FP64 solve through gfp_solve_noalloc.
 

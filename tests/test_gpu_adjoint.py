@@ -29,6 +29,26 @@ def test_autograd_backward_matches_oracle_closed_form():
         assert abs(c.item() - rJ.sigma_mean[I]) <= 1e-9 * abs(rJ.sigma_mean[I]) + 1e-14
 
 
+def test_gradient_32_lognormal_matches_oracle_gradient():
+    """The adjoint configuration scaled to 32^3 (cube of edge 16, contrast 10, lognormal(0.1) Lame fields):
+    dC_1111/dlambda and /dmu of every voxel from gfp_grad against the oracle's gradient (its closed-form
+    contraction of its own converged fields), 1e-7 relative."""
+    from paper_2009_03762_gb300 import gfp
+    n = 32
+    lam, mu = M.sharp_cube(n, 16, 1.0, 10.0)
+    lam, mu = M.lognormal_perturb(lam, mu, sigma=0.1, seed=5)
+    ref = O.default_reference(lam, mu)
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu, ref=ref)
+    dl, dm = g.grad(gfp.scheme("AFB_R"), 0, 0, 1e-13, 20000)
+    r = O.solve(lam, mu, "AFB_R", [1.0, 0, 0, 0, 0, 0], tol=1e-13, maxit=20000, ref=ref)
+    assert r.converged
+    ol, om = O.gradient_closed_form(r.eps, r.eps)
+    np.testing.assert_allclose(dl, ol, rtol=1e-7, atol=1e-7 * np.abs(ol).max())
+    np.testing.assert_allclose(dm, om, rtol=1e-7, atol=1e-7 * np.abs(om).max())
+    g.close()
+
+
 def test_adjoint_128_lognormal_against_finite_differences():
     """128^3 cube (edge 64, contrast 10) with lognormal(0.1) Lame fields: dC_1111/dmu and /dlambda from the
     adjoint contraction against central differences (relative step 1e-6, FP64) on 16 seeded voxels."""

@@ -96,3 +96,40 @@ def test_laminate_512_along_x3_closed_form(gfp):
     s13 = E[4] / np.mean(1 / (2 * m3))
     np.testing.assert_allclose([r.sigma_mean[2], r.sigma_mean[4]], [s33, s13], rtol=1e-6)
     g.close()
+
+
+def test_c_eff_256_mixed_matches_fp64_full_matrix(gfp):
+    """The 256^3 random-sphere cell (volume fraction 0.25, radii U[6, 16], contrast 100, PCD AFB/R): the
+    full 6 x 6 effective stiffness from six mixed-precision solves to eta < 1e-8 against six FP64 GPU
+    solves, within 1e-6 relative (the mixed-precision bar)."""
+    n = 256
+    lam, mu = M.random_spheres(n, vf=0.25, rmin=6.0, rmax=16.0, contrast=100.0, seed=0)
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu)
+    g.set_tiles(gfp.MIXED, BENCH_TILES)
+    Cm, itm, rcm = g.effective_stiffness(gfp.scheme("AFB_R", "PCD", "MIXED"), 1e-8, 20000)
+    C64, it64, rc64 = g.effective_stiffness(gfp.scheme("AFB_R", "PCD", "FP64"), 1e-8, 20000)
+    assert rcm == 0 and rc64 == 0
+    assert np.abs(Cm - C64).max() / np.abs(C64).max() <= 1e-6, (Cm, C64)
+    # cubic-symmetric in the mean: the matrix is symmetric to the solver tolerance
+    assert np.abs(C64 - C64.T).max() / np.abs(C64).max() <= 1e-6
+    g.close()
+
+
+def test_random_spheres_512_mixed_matches_fp64(gfp):
+    """512^3 random-sphere cell of the mixed-precision configuration (volume fraction 0.25, radii U[6, 16],
+    contrast 100, seed 0): the shear load's mean stress from the mixed solve against the FP64 GPU solve
+    (1e-6 relative), and the FP64 mean strain held by the mixed solve."""
+    n = 512
+    lam, mu = M.random_spheres(n, vf=0.25, rmin=6.0, rmax=16.0, contrast=100.0, seed=0)
+    E = [0.0, 0.0, 0.0, 0.0, 0.0, 0.5]
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu)
+    sch = gfp.scheme("AFB_R", "PCD", "MIXED")
+    g.tune(sch, iters=2)
+    rm = g.solve(sch, E, 1e-8, 20000)
+    assert rm.converged and rm.residual < 1e-8
+    r64 = g.solve(gfp.scheme("AFB_R", "PCD", "FP64"), E, 1e-8, 20000)
+    assert r64.converged
+    assert _rel(rm.sigma_mean, r64.sigma_mean) <= 1e-6
+    g.close()
