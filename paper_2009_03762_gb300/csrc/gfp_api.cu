@@ -173,17 +173,19 @@ __global__ void corr_mean_final_kernel(const double* __restrict__ part, int nb, 
 __constant__ int c_mono4[3][3][3][3];  // index of the degree-4 monomial k_i k_j k_a k_b
 __constant__ int c_mono2[3][3];        // index of the degree-2 monomial k_a k_b
 
-__global__ void dgo_table_kernel(double* __restrict__ tab, Dims d, const double* __restrict__ w1,
-                                 const double* __restrict__ w2, const double* __restrict__ w3, int m1, int m2, int m3,
-                                 double h, double lam_h, double mu_h) {
-  const long long npts = (long long)d.n1h * d.n2 * d.n3;
+// Alias sums of Gamma^c at the representative points rep_pts (o1, o2, o3) packed as o1 | o2 << 11 | o3 << 22:
+// the 21 Mandel entries of each into rep [21][F3][F2][F1] (F_r = n_r/2 + 1) at (o1, o2, o3).
+__global__ void dgo_table_kernel(double* __restrict__ rep, const int* __restrict__ rep_pts, int nrep, Dims d,
+                                 const double* __restrict__ w1, const double* __restrict__ w2,
+                                 const double* __restrict__ w3, int m1, int m2, int m3, double h, double lam_h,
+                                 double mu_h) {
   const double two_pi = 6.283185307179586476925;
   const double cc = (lam_h + mu_h) / (lam_h + 2.0 * mu_h);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < npts;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int o1 = (int)(idx % d.n1h);
-    const long long rest = idx / d.n1h;
-    const int o2 = (int)(rest % d.n2), o3 = (int)(rest / d.n2);
+  const int F1 = d.n1 / 2 + 1, F2 = d.n2 / 2 + 1, F3 = d.n3 / 2 + 1;
+  const long long RS = (long long)F1 * F2 * F3;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nrep; idx += gridDim.x * blockDim.x) {
+    const int code = rep_pts[idx];
+    const int o1 = code & 2047, o2 = (code >> 11) & 2047, o3 = (code >> 22) & 2047;
     double S2[6] = {0, 0, 0, 0, 0, 0};
     double S4[15];
     for (int q = 0; q < 15; ++q) S4[q] = 0.0;
@@ -236,8 +238,7 @@ __global__ void dgo_table_kernel(double* __restrict__ tab, Dims d, const double*
     const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
     auto s2 = [&](int a, int b) { return S2[c_mono2[a][b]]; };
     auto dl = [](int a, int b) { return a == b ? 1.0 : 0.0; };
-    const long long S = d.S;
-    const long long pos = d.row(o3, o2) * d.P + o1;
+    const long long pos = ((long long)o3 * F2 + o2) * F1 + o1;
     int q = 0;
     for (int P = 0; P < 6; ++P)
       for (int Q = P; Q < 6; ++Q, ++q) {
@@ -246,7 +247,52 @@ __global__ void dgo_table_kernel(double* __restrict__ tab, Dims d, const double*
                        (4.0 * mu_h) +
                    cc / mu_h * S4[c_mono4[i][j][a][b]];
         const double f = (P < 3 ? 1.0 : 1.41421356237309504880) * (Q < 3 ? 1.0 : 1.41421356237309504880);
-        tab[q * S + pos] = (o1 == 0 && o2 == 0 && o3 == 0) ? 0.0 : f * g;
+        rep[q * RS + pos] = (o1 == 0 && o2 == 0 && o3 == 0) ? 0.0 : f * g;
+      }
+  }
+}
+
+// The table at every half-spectrum point from the representatives.  Axis r folds to
+// f_r = min(o_r, n_r - o_r): the alias sum of n_r - o_r runs over the same terms with k_r negated
+// (nu_r -> -nu_r - 1 keeps the weight), so an entry with tensor indices (i, j, a, b) takes the sign
+// s_i s_j s_a s_b, s_r = -1 on folded axes.  On a cubic grid (`cubic`: equal lengths and alias ranges)
+// the folded point is sorted, g = (f_sig(0), f_sig(1), f_sig(2)) ascending, and the isotropic Gamma_H
+// gives Gamma^c(f)_ijab = Gamma^c(g)_{pi(i) pi(j) pi(a) pi(b)} with pi the inverse of sig.
+__global__ void dgo_expand_kernel(double* __restrict__ tab, const double* __restrict__ rep, Dims d, int cubic) {
+  const int F1 = d.n1 / 2 + 1, F2 = d.n2 / 2 + 1, F3 = d.n3 / 2 + 1;
+  const long long RS = (long long)F1 * F2 * F3;
+  const long long npts = (long long)d.n1h * d.n2 * d.n3;
+  const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
+  const int mandel[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < npts;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int o[3] = {(int)(idx % d.n1h), (int)((idx / d.n1h) % d.n2), (int)(idx / ((long long)d.n1h * d.n2))};
+    const int n[3] = {d.n1, d.n2, d.n3};
+    int f[3], sg[3];
+    for (int r = 0; r < 3; ++r) {
+      const bool fold = o[r] > n[r] / 2;
+      f[r] = fold ? n[r] - o[r] : o[r];
+      sg[r] = fold ? -1 : 1;
+    }
+    int pi[3] = {0, 1, 2};  // axis r of f is axis pi[r] of the representative
+    int g[3] = {f[0], f[1], f[2]};
+    if (cubic) {
+      int sig[3] = {0, 1, 2};  // g[k] = f[sig[k]], ascending
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2 - a; ++b)
+          if (f[sig[b]] > f[sig[b + 1]]) { const int t = sig[b]; sig[b] = sig[b + 1]; sig[b + 1] = t; }
+      for (int k = 0; k < 3; ++k) { g[k] = f[sig[k]]; pi[sig[k]] = k; }
+    }
+    const long long rpos = ((long long)g[2] * F2 + g[1]) * F1 + g[0];
+    const long long pos = d.row(o[2], o[1]) * d.P + o[0];
+    int q = 0;
+    for (int P = 0; P < 6; ++P)
+      for (int Q = P; Q < 6; ++Q, ++q) {
+        const int i = vi[P], j = vj[P], a = vi[Q], b = vj[Q];
+        int P2 = mandel[pi[i]][pi[j]], Q2 = mandel[pi[a]][pi[b]];
+        if (P2 > Q2) { const int t = P2; P2 = Q2; Q2 = t; }
+        const int q2 = P2 * 6 - P2 * (P2 - 1) / 2 + (Q2 - P2);  // upper-triangle index of (P2, Q2)
+        tab[q * d.S + pos] = (double)(sg[i] * sg[j] * sg[a] * sg[b]) * rep[q2 * RS + rpos];
       }
   }
 }
@@ -1031,12 +1077,32 @@ int ensure_dgo(gfp_grid g, int dgo_m) {
     GFP_CU(cudaMemcpy(w[r], hw.data(), sizeof(double) * hw.size(), cudaMemcpyHostToDevice));
   }
   GFP_CU(cudaMemsetAsync(g->dgo, 0, sizeof(double) * 21 * (size_t)d.S, g->stream));
-  const long long npts = (long long)d.n1h * d.n2 * d.n3;
-  dgo_table_kernel<<<(int)std::min<long long>(4096, (npts + 127) / 128), 128, 0, g->stream>>>(
-      g->dgo, d, w[0], w[1], w[2], ms[0], ms[1], ms[2], g->h, g->lam_h, g->mu_h);
-  g->launches += 1;
-  cudaError_t e = cudaGetLastError();
+  // representatives: every axis folded to [0, n_r/2]; on a cubic grid also sorted ascending
+  const bool cubic = ns[0] == ns[1] && ns[1] == ns[2] && ms[0] == ms[1] && ms[1] == ms[2];
+  const int F[3] = {ns[0] / 2 + 1, ns[1] / 2 + 1, ns[2] / 2 + 1};
+  std::vector<int> pts;
+  for (int o3 = 0; o3 < F[2]; ++o3)
+    for (int o2 = 0; o2 < F[1]; ++o2)
+      for (int o1 = 0; o1 < F[0]; ++o1)
+        if (!cubic || (o1 <= o2 && o2 <= o3)) pts.push_back(o1 | (o2 << 11) | (o3 << 22));
+  double* rep = nullptr;
+  int* dpts = nullptr;
+  cudaError_t e = cudaMalloc(&rep, sizeof(double) * 21 * (size_t)F[0] * F[1] * F[2]);
+  if (e == cudaSuccess) e = cudaMalloc(&dpts, sizeof(int) * pts.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dpts, pts.data(), sizeof(int) * pts.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int nrep = (int)pts.size();
+    dgo_table_kernel<<<std::max(1, std::min(4096, (nrep + 63) / 64)), 64, 0, g->stream>>>(
+        rep, dpts, nrep, d, w[0], w[1], w[2], ms[0], ms[1], ms[2], g->h, g->lam_h, g->mu_h);
+    const long long npts = (long long)d.n1h * d.n2 * d.n3;
+    dgo_expand_kernel<<<(int)std::min<long long>(4096, (npts + 255) / 256), 256, 0, g->stream>>>(g->dgo, rep, d,
+                                                                                                  cubic ? 1 : 0);
+    g->launches += 2;
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  cudaFree(rep);
+  cudaFree(dpts);
   for (int r = 0; r < 3; ++r) cudaFree(w[r]);
   if (e != cudaSuccess) { note_error(e, __LINE__); return cuda_status(e); }
   g->dgo_key[0] = g->lam_h;

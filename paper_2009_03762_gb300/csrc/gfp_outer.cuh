@@ -63,13 +63,15 @@ __global__ void __launch_bounds__(kResTX * kResTY) residual64_kernel(const doubl
   const bool col_ok = (x0 + tx < n1) && (y0 + ty < n2);
   const int nz = min(kResTZ, n3 - z0);
   double ss[6] = {0, 0, 0, 0, 0, 0};
-  double rr = 0.0;
+  float rr = 0.f;  // eta needs relative accuracy only; r itself is FP64
+  // the averaged forward differences need the halo on the high side only
+  constexpr int LO = S == RS_AFD ? 1 : 0, RW = HX - LO, RH = HY - LO;
 #pragma unroll 1
-  for (int p = 0; p < nz + 2; ++p) {
+  for (int p = S == RS_AFD ? 1 : 0; p < nz + 2; ++p) {
     const int zw = ((z0 - 1 + p) % n3 + n3) % n3;
     const int slot = p % 3;
-    for (int i = threadIdx.x; i < HX * HY; i += NT) {
-      const int hx = i % HX, hy = i / HX;
+    for (int i = threadIdx.x; i < RW * RH; i += NT) {
+      const int hx = LO + i % RW, hy = LO + i / RW;
       const int xg = ((x0 - 1 + hx) % n1 + n1) % n1;
       const int yg = ((y0 - 1 + hy) % n2 + n2) % n2;
       const long long v = ((long long)zw * n2 + yg) * n1 + xg;
@@ -112,6 +114,34 @@ __global__ void __launch_bounds__(kResTX * kResTY) residual64_kernel(const doubl
         o[(jj + 2) % 3] = ob;
         return f(c, o[0], o[1], o[2]);
       };
+      const double sc = (S == RS_CD ? 0.5 : (S == RS_ACD ? 0.125 : 0.25)) * inv_h;
+      double r1, r2, r3;
+      if (S == RS_AFD) {
+        // over the unit cube, with the pair sums along the third axis shared by a component's two
+        // derivatives: D_u f = [p(1,0) + p(1,1)] - [p(0,0) + p(0,1)], p(a,b) = f(a,b,0) + f(a,b,1)
+        auto one = [&](int c, int u) -> double {  // single derivative along axis u
+          const double hi = (at(c, u, 1, 0, 0) + at(c, u, 1, 0, 1)) + (at(c, u, 1, 1, 0) + at(c, u, 1, 1, 1));
+          const double lo = (at(c, u, 0, 0, 0) + at(c, u, 0, 0, 1)) + (at(c, u, 0, 1, 0) + at(c, u, 0, 1, 1));
+          return hi - lo;
+        };
+        // two derivatives along u and v = (u + 1) % 3 of component c, sharing the sums along w
+        auto two = [&](int c, int u, double& du, double& dv) {
+          double q[2][2];
+#pragma unroll
+          for (int a = 0; a <= 1; ++a)
+#pragma unroll
+            for (int b = 0; b <= 1; ++b) q[a][b] = at(c, u, a, b, 0) + at(c, u, a, b, 1);
+          du = (q[1][0] + q[1][1]) - (q[0][0] + q[0][1]);
+          dv = (q[0][1] + q[1][1]) - (q[0][0] + q[1][0]);
+        };
+        double d12x, d12y, d23y, d23z, d13z, d13x;
+        two(5, 0, d12x, d12y);  // sigma_12: D_1, D_2
+        two(3, 1, d23y, d23z);  // sigma_23: D_2, D_3
+        two(4, 2, d13z, d13x);  // sigma_13: D_3, D_1
+        r1 = sc * (one(0, 0) + d12y + d13z);
+        r2 = sc * (d12x + one(1, 1) + d23z);
+        r3 = sc * (d13x + d23y + one(2, 2));
+      } else {
       // D_j of component c, unscaled
       auto D = [&](int c, int jj) -> double {
         double acc = 0.0;
@@ -130,21 +160,22 @@ __global__ void __launch_bounds__(kResTX * kResTY) residual64_kernel(const doubl
         }
         return acc;
       };
-      const double sc = (S == RS_CD ? 0.5 : (S == RS_ACD ? 0.125 : 0.25)) * inv_h;
       // components (11, 22, 33, 23, 13, 12) = (0, 1, 2, 3, 4, 5)
-      const double r1 = sc * (D(0, 0) + D(5, 1) + D(4, 2));
-      const double r2 = sc * (D(5, 0) + D(1, 1) + D(3, 2));
-      const double r3 = sc * (D(4, 0) + D(3, 1) + D(2, 2));
+      r1 = sc * (D(0, 0) + D(5, 1) + D(4, 2));
+      r2 = sc * (D(5, 0) + D(1, 1) + D(3, 2));
+      r3 = sc * (D(4, 0) + D(3, 1) + D(2, 2));
+      }
       const long long v = ((long long)(z0 + p - 2) * n2 + (y0 + ty)) * n1 + (x0 + tx);
-      rout[v] = (float)r1;
-      rout[N + v] = (float)r2;
-      rout[2 * N + v] = (float)r3;
-      rr += r1 * r1 + r2 * r2 + r3 * r3;
+      const float f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+      rout[v] = f1;
+      rout[N + v] = f2;
+      rout[2 * N + v] = f3;
+      rr += f1 * f1 + f2 * f2 + f3 * f3;
     }
     __syncthreads();
   }
   // per-CTA sums, fixed order
-  double q[7] = {rr, ss[0], ss[1], ss[2], ss[3], ss[4], ss[5]};
+  double q[7] = {(double)rr, ss[0], ss[1], ss[2], ss[3], ss[4], ss[5]};
 #pragma unroll
   for (int k = 0; k < 7; ++k)
     for (int off = 16; off > 0; off >>= 1) q[k] += __shfl_down_sync(0xffffffffu, q[k], off);
