@@ -200,6 +200,16 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
                       const double* ref_lambda_mu, const gfp_scheme* scheme, const double E_macro[6], double tol,
                       int maxit, double* eps, gfp_result* out, void* cuda_stream);
 
+/* Measurement hook (no counterpart in the paper): the peak fused multiply-add rate of the current GPU,
+ * in TFLOP/s (2 flops per FMA), from eight independent FMA chains per thread over 8 CTAs of 256 threads
+ * per SM, best of three timed launches after one warm-up, on the legacy default stream.
+ *   dtype   0: FP64, 1: FP32
+ *   tflops  out: the measured rate
+ * Used as the denominator of the FP64 path's arithmetic roofline (its transforms are bound by the FP64
+ * units on this GPU).  Returns GFP_ERR_ARG for other dtypes or a null pointer, GFP_ERR_CUDA on a CUDA
+ * error; allocates and frees a small device buffer. */
+int gfp_measure_fma_peak(int dtype, double* tflops);
+
 /* Static message for a status code. */
 const char* gfp_error_string(int status);
 

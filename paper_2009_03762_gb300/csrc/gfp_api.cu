@@ -415,6 +415,24 @@ __global__ void batch_status_kernel(SolveState* const* __restrict__ sts, int n, 
 
 }  // namespace gfp
 
+// Peak FMA throughput (measurement hook): eight independent FMA chains per thread, values kept bounded
+// (x <- a x + b with a < 1 converges), the sum stored only under a condition the values never meet so
+// that the chains stay live.
+template <typename R>
+__global__ void fma_peak_kernel(R* __restrict__ sink, int iters, R a, R b) {
+  R x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = (R)(threadIdx.x + c) * (R)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  R t = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) t += x[c];
+  if (t == (R)-1) sink[blockIdx.x] = t;
+}
+
 // ------------------------------------------------------------------------------- the grid
 struct gfp_grid_s {
   int n1, n2, n3;
@@ -1640,6 +1658,39 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
   for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
   for (int k = 0; k < 5; ++k) pass_ms[k] = acc[k] / iters;
   GFP_CU(cudaGetLastError());
+  return GFP_OK;
+}
+
+// Peak FMA rate of this GPU in TFLOP/s (see include/gfp.h).
+int gfp_measure_fma_peak(int dtype, double* tflops) {
+  if (!tflops || (dtype != 0 && dtype != 1)) return GFP_ERR_ARG;
+  int dev = 0, sms = 0;
+  GFP_CU(cudaGetDevice(&dev));
+  GFP_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256;
+  const int iters = dtype == 0 ? 4000 : 200000;
+  void* sink = nullptr;
+  GFP_CU(cudaMalloc(&sink, sizeof(double) * blocks));
+  cudaEvent_t e0, e1;
+  GFP_CU(cudaEventCreate(&e0));
+  GFP_CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first run warms up
+    cudaEventRecord(e0, 0);
+    if (dtype == 0) fma_peak_kernel<double><<<blocks, threads>>>((double*)sink, iters, 0.999999, 1e-6);
+    else fma_peak_kernel<float><<<blocks, threads>>>((float*)sink, iters, 0.999f, 1e-3f);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  const cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  GFP_CU(e);
+  *tflops = 2.0 * 8.0 * (double)blocks * threads * (double)iters / (best * 1e-3) / 1e12;
   return GFP_OK;
 }
 

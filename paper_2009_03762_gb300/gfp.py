@@ -46,7 +46,8 @@ _lib = None
 EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "gfp_effective_stiffness",
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
            "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
-           "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain", "gfp_get_displacement")
+           "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain", "gfp_get_displacement",
+           "gfp_measure_fma_peak")
 
 
 def lib():
@@ -76,6 +77,7 @@ def lib():
     L.gfp_tune.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
     L.gfp_solve_batch.argtypes = [ip, vp, ctypes.POINTER(Scheme), dp, ip, vp, vp]
     L.gfp_set_fault_injection.argtypes = [ip, ip]
+    L.gfp_measure_fma_peak.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
     L.gfp_set_eigenstrain.argtypes = [vp, vp, ip]
     L.gfp_get_displacement.argtypes = [vp, ctypes.POINTER(Scheme), vp, ip]
@@ -320,6 +322,13 @@ def solve_batch(grids, sch, tol=1e-8, maxit=5000):
                                C.ctypes.data_as(ctypes.c_void_p), its.ctypes.data_as(ctypes.c_void_p))
     _check(rc, "gfp_solve_batch", ok=(0, -4))
     return C.reshape(count, 6, 6), its, rc
+
+
+def measure_fma_peak(dtype="f64"):
+    """Peak FMA rate of the current GPU in TFLOP/s (gfp_measure_fma_peak), dtype "f64" or "f32"."""
+    v = ctypes.c_double(0.0)
+    _check(lib().gfp_measure_fma_peak(0 if dtype == "f64" else 1, ctypes.byref(v)), "gfp_measure_fma_peak")
+    return v.value
 
 
 def batch_shard(costs, rank, world):
