@@ -897,7 +897,7 @@ void outer_pass64(cudaStream_t s, const Dims& d, double h, int op, double* eps, 
   switch (res_stencil(op)) {
     case RS_CD: residual64_kernel<RS_CD><<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
     case RS_ACD: residual64_kernel<RS_ACD><<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
-    default: residual64_kernel<RS_AFD><<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
+    default: residual64_afd_kernel<<<grid, kResTX * kResTY, 0, s>>>(eps, lam, mu, estar, d, inv_h, rbuf, rpart, st); break;
   }
   res64_sum_kernel<<<1, 256, 0, s>>>(rpart, res64_blocks(d), d.N, st, partials);
   launch_reduce_eta(s, partials, 1, st, nullptr, 0);

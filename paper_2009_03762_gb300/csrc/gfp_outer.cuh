@@ -192,6 +192,111 @@ __global__ void __launch_bounds__(kResTX * kResTY) residual64_kernel(const doubl
   }
 }
 
+// The averaged-forward-difference case (AHC, AFB/R) of residual64_kernel with the work shared between
+// planes.  In the 2x2 window of a thread on plane z, with g_ab = f(x + a, y + b, z):
+//   Qx f = (g10 - g00) + (g11 - g01),  Qy f = (g01 - g00) + (g11 - g10),  P f = g00 + g01 + g10 + g11,
+// and D_x f(z) = Qx f(z) + Qx f(z+1), D_y f(z) = Qy f(z) + Qy f(z+1), D_z f(z) = P f(z+1) - P f(z).  So
+// r_1(z) = M_1(z) + S_1(z+1) with S_1 = Qx s11 + Qy s12 + P s13 and M_1 = Qx s11 + Qy s12 - P s13 (and
+// likewise r_2 from s12, s22, s23 and r_3 from s13, s23, s33): each plane is visited once, and only M
+// is carried to the next plane.  Same outputs and partial sums as residual64_kernel<RS_AFD>.
+__global__ void __launch_bounds__(kResTX * kResTY) residual64_afd_kernel(const double* __restrict__ eps,
+                                                                         const double* __restrict__ lam,
+                                                                         const double* __restrict__ mu,
+                                                                         const double* __restrict__ estar, Dims d,
+                                                                         double inv_h, float* __restrict__ rout,
+                                                                         double* __restrict__ part,
+                                                                         const SolveState* gate) {
+  if (gate && gate->done) return;
+  constexpr int HX = kResTX + 1, HY = kResTY + 1, NT = kResTX * kResTY;
+  __shared__ double sg[6][HY][HX];
+  __shared__ double red[NT / 32][8];
+  const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+  const long long N = d.N;
+  const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY, z0 = blockIdx.z * kResTZ;
+  const int tx = threadIdx.x % kResTX, ty = threadIdx.x / kResTX;
+  const bool col_ok = (x0 + tx < n1) && (y0 + ty < n2);
+  const int nz = min(kResTZ, n3 - z0);
+  const double sc = 0.25 * inv_h;
+  double ss[6] = {0, 0, 0, 0, 0, 0};
+  float rr = 0.f;
+  double M1 = 0.0, M2 = 0.0, M3 = 0.0;
+#pragma unroll 1
+  for (int p = 0; p <= nz; ++p) {  // planes z0 .. z0 + nz
+    const int zw = (z0 + p) % n3;
+    for (int i = threadIdx.x; i < HX * HY; i += NT) {
+      const int hx = i % HX, hy = i / HX;
+      const int xg = (x0 + hx) % n1, yg = (y0 + hy) % n2;
+      const long long v = ((long long)zw * n2 + yg) * n1 + xg;
+      double e[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] = eps[c * N + v];
+      if (estar) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] -= estar[c * N + v];
+      }
+      const double m2 = 2.0 * mu[v], ltr = lam[v] * (e[0] + e[1] + e[2]);
+      double sgm[6];
+      sgm[0] = m2 * e[0] + ltr;
+      sgm[1] = m2 * e[1] + ltr;
+      sgm[2] = m2 * e[2] + ltr;
+      sgm[3] = m2 * e[3];
+      sgm[4] = m2 * e[4];
+      sgm[5] = m2 * e[5];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sg[c][hy][hx] = sgm[c];
+      if (hx < kResTX && hy < kResTY && p < nz && x0 + hx < n1 && y0 + hy < n2) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ss[c] += sgm[c];
+      }
+    }
+    __syncthreads();
+    if (col_ok) {
+      auto g = [&](int c, int a, int b) -> double { return sg[c][ty + b][tx + a]; };
+      // components (11, 22, 33, 23, 13, 12) = (0, 1, 2, 3, 4, 5)
+      const double qx11 = (g(0, 1, 0) - g(0, 0, 0)) + (g(0, 1, 1) - g(0, 0, 1));
+      const double qy22 = (g(1, 0, 1) - g(1, 0, 0)) + (g(1, 1, 1) - g(1, 1, 0));
+      const double p33 = (g(2, 0, 0) + g(2, 0, 1)) + (g(2, 1, 0) + g(2, 1, 1));
+      const double a12 = g(5, 1, 1) - g(5, 0, 0), b12 = g(5, 1, 0) - g(5, 0, 1);
+      const double qx12 = a12 + b12, qy12 = a12 - b12;
+      const double u13 = g(4, 1, 0) + g(4, 1, 1), w13 = g(4, 0, 0) + g(4, 0, 1);
+      const double qx13 = u13 - w13, p13 = u13 + w13;
+      const double u23 = g(3, 0, 1) + g(3, 1, 1), w23 = g(3, 0, 0) + g(3, 1, 0);
+      const double qy23 = u23 - w23, p23 = u23 + w23;
+      const double t1 = qx11 + qy12, t2 = qx12 + qy22, t3 = qx13 + qy23;
+      if (p >= 1) {  // outputs on plane z0 + p - 1
+        const double r1 = sc * (M1 + (t1 + p13));
+        const double r2 = sc * (M2 + (t2 + p23));
+        const double r3 = sc * (M3 + (t3 + p33));
+        const long long v = ((long long)(z0 + p - 1) * n2 + (y0 + ty)) * n1 + (x0 + tx);
+        const float f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+        rout[v] = f1;
+        rout[N + v] = f2;
+        rout[2 * N + v] = f3;
+        rr += f1 * f1 + f2 * f2 + f3 * f3;
+      }
+      M1 = t1 - p13;
+      M2 = t2 - p23;
+      M3 = t3 - p33;
+    }
+    __syncthreads();
+  }
+  double q[7] = {(double)rr, ss[0], ss[1], ss[2], ss[3], ss[4], ss[5]};
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+    for (int off = 16; off > 0; off >>= 1) q[k] += __shfl_down_sync(0xffffffffu, q[k], off);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[threadIdx.x >> 5][k] = q[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double sm = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sm += red[w][threadIdx.x];
+    const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[8 * b + threadIdx.x] = sm;
+  }
+}
+
 // Sum of the per-CTA residual sums in a fixed order: st->T0 = sum sigma (the transform at k = 0) and
 // out[0] = N sum |r|^2, the spectral residual sum that reduce_eta turns into eta and the decision.
 __global__ void res64_sum_kernel(const double* __restrict__ part, int np, long long N, SolveState* st,

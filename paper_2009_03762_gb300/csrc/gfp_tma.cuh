@@ -272,42 +272,41 @@ __device__ __forceinline__ void rot_right(V* a, int s) {
   }
 }
 
-// T x T transpose among the T consecutive lanes t of a group (T a power of two dividing 32): on entry
-// v[i] is the element this lane holds for lane i, on return v[s] is the element lane s held for this
-// lane.  The registers are rotated by the lane index before and after, so that in round j every lane
-// sends the same register j (to lane (t - j) mod T) and receives from lane (t + j) mod T.
-template <int T_, typename V>
-__device__ __forceinline__ void lane_transpose(V* v, int t) {
-  V u[T_];
-#pragma unroll
-  for (int j = 0; j < T_; ++j) u[j] = v[(T_ - j) % T_];
-  rot_right<T_>(u, t);  // u[j] = v[(t - j) mod T]
-#pragma unroll
-  for (int j = 1; j < T_; ++j) {
-    const int src = (t + j) & (T_ - 1);
-    V w;
-    w.x = __shfl_sync(0xffffffffu, u[j].x, src, T_);
-    w.y = __shfl_sync(0xffffffffu, u[j].y, src, T_);
-    u[j] = w;  // the element lane (t + j) mod T holds for this lane
-  }
-  rot_right<T_>(u, t);
-#pragma unroll
-  for (int j = 0; j < T_; ++j) v[j] = u[j];
-}
-
-// Line transform of length N = T^2 on the T lanes of a group (Stockham, two radix-T stages, the
-// exchange by lane_transpose).  On entry v[r] = x[t + T r]; on return v[k] = X[t + T k].
+// Line transform of length N = T^2 on the T lanes of a group (Stockham, two radix-T stages, one
+// exchange of T shuffle rounds).  On entry v[r] = x[t + T r]; on return v[k] = X[t + T k].
+// Stage 0 gives lane t the values y_k = sum_m x[t + T m] w^{m k} (w = w_T, the transform's sign), of
+// which y_k is lane k's stage-1 input t.  The exchange needs them rotated by the lane, u_j = y_{(t - j)
+// mod T}, so that round j can send one register j to every lane; instead of moving registers, the
+// rotation is computed: y_{t - j} = sum_m (x_m w^{m t}) w^{-m j}, a transform of the opposite sign of
+// the inputs scaled by w^{m t}.  After round j lane t holds in register j the stage-1 input from
+// position (t + j) mod T (already multiplied by its twiddle w_N^{s t} at the sender), which a register
+// rotation by t puts in order.  Tables in shared memory, read by consecutive lanes at compile-time
+// offsets: rt[m T + t] = w_T^{m t} and tw3[j T + t] = w_N^{t ((t - j) mod T)} (forward sign).
 template <int N, bool INV>
-__device__ __forceinline__ void sfft(float2* v, int t, const float2* __restrict__ tw) {
-  constexpr int T_ = CPlan<N>::T;
-  Dft<T_, INV, float2>::run(v);  // v[k] = y[T t + k], the element lane k needs for its stage-1 input t
+__device__ __forceinline__ void sfft(float2* v, int t, int h, const float2* tw3, const float2* rt) {
+  constexpr int T_ = CPlan<N>::T, LPW = 32 / T_;
 #pragma unroll
-  for (int k = 1; k < T_; ++k) {  // stage-1 twiddle w_N^{t k} of that element, applied by its sender
-    float2 w = tw[t * k];
+  for (int m = 1; m < T_; ++m) {  // x_m w^{m t}
+    float2 w = rt[m * T_ + t];
     if (INV) w.y = -w.y;
-    v[k] = cmul(v[k], w);
+    v[m] = cmul(v[m], w);
   }
-  lane_transpose<T_>(v, t);        // v[s] = y[T s + t] (times its twiddle) = stage-1 input s
+  Dft<T_, !INV, float2>::run(v);  // v[j] = y_{(t - j) mod T}, destined to lane (t - j) mod T
+#pragma unroll
+  for (int j = 0; j < T_; ++j) {  // its stage-1 twiddle w_N^{t (t - j)}
+    float2 w = tw3[j * T_ + t];
+    if (INV) w.y = -w.y;
+    v[j] = cmul(v[j], w);
+  }
+#pragma unroll
+  for (int j = 1; j < T_; ++j) {  // round j: from position (t + j) mod T, its register j
+    const int src = LPW * ((t + j) & (T_ - 1)) + h;
+    float2 w;
+    w.x = __shfl_sync(0xffffffffu, v[j].x, src);
+    w.y = __shfl_sync(0xffffffffu, v[j].y, src);
+    v[j] = w;
+  }
+  rot_right<T_>(v, t);  // v[s] = stage-1 input s
   Dft<T_, INV, float2>::run(v);
 }
 
@@ -325,7 +324,9 @@ template <int N> struct SPlanOk {
   static constexpr bool ok = CPlan<N>::ok && CPlan<N>::NST == 2 && CPlan<N>::R(0) == CPlan<N>::T &&
                              CPlan<N>::R(1) == CPlan<N>::T && CPlan<N>::E == CPlan<N>::T && N <= 256;
 };
-template <int N> constexpr size_t zs_smem_bytes() { return (size_t)6 * N * 64 + 1024 + (size_t)2 * N * sizeof(float2); }
+template <int N> constexpr size_t zs_smem_bytes() {
+  return (size_t)6 * N * 64 + 1024 + (size_t)3 * N * sizeof(float2);
+}
 
 template <int N>
 __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -342,6 +343,7 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
   unsigned char* tile = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float2* twl = reinterpret_cast<float2*>(tile + 6 * N * 64);
   float2* ab3 = twl + N;
+  float2* roots = ab3 + N;
   __shared__ __align__(8) unsigned long long bar;
   __shared__ double red[32];
   __shared__ int abort_flag;
@@ -357,7 +359,9 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
     for (int c = 0; c < 6; ++c) tma_load_4d(tile + c * N * 64, &tmap, &bar, 2 * k10, k2, 0, c);
   }
   for (int i = threadIdx.x; i < N; i += NT) {
-    twl[i] = tw[i];
+    const int tt = i % T_, jj = i / T_;
+    twl[i] = tw[tt * ((tt - jj + T_) % T_)];        // twl[j T + t] = w_N^{t ((t - j) mod T)}
+    roots[i] = tw[T_ * ((tt * jj) % T_)];            // roots[m T + t] = w_T^{m t} = w_N^{T (m t mod T)}
     float2 ab;
     ab.x = gp.A[2][i];
     ab.y = gp.B[2][i];
@@ -372,19 +376,22 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
     }
     return;
   }
-  const int t = threadIdx.x & (T_ - 1), line = threadIdx.x / T_;
+  // lines interleaved in the warp: lane = LPW t + h, line = LPW warp + h
+  constexpr int LPW = 32 / T_;
+  const int lane = threadIdx.x & 31, h = lane % LPW, t = lane / LPW;
+  const int line = (threadIdx.x >> 5) * LPW + h;
   const int col = line % COLS, compA = line / COLS;
   auto el = [&](int c, int z, int cc) -> float2& {
     return *reinterpret_cast<float2*>(tile + swz64((unsigned)(c * N * 64 + z * 64 + cc * 8)));
   };
   // forward transforms of lines A and B, in place (each thread owns rows t + T r of its lines)
 #pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    const int c = compA + 3 * h;
+  for (int ab = 0; ab < 2; ++ab) {
+    const int c = compA + 3 * ab;
     float2 v[T_];
 #pragma unroll
     for (int r = 0; r < T_; ++r) v[r] = el(c, t + T_ * r, col);
-    sfft<N, false>(v, t, twl);
+    sfft<N, false>(v, t, h, twl, roots);
 #pragma unroll
     for (int k = 0; k < T_; ++k) el(c, t + T_ * k, col) = v[k];
   }
@@ -452,12 +459,12 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
   }
   // inverse transforms, in place
 #pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    const int c = compA + 3 * h;
+  for (int ab = 0; ab < 2; ++ab) {
+    const int c = compA + 3 * ab;
     float2 v[T_];
 #pragma unroll
     for (int r = 0; r < T_; ++r) v[r] = el(c, t + T_ * r, col);
-    sfft<N, true>(v, t, twl);
+    sfft<N, true>(v, t, h, twl, roots);
 #pragma unroll
     for (int k = 0; k < T_; ++k) el(c, t + T_ * k, col) = v[k];
   }
