@@ -73,16 +73,23 @@ typedef struct {
   int dgo_m;      /* DGO alias half-range m (<= 0: n_r / 2 per axis, at least 1) */
   int prec;       /* gfp_prec: FP64 throughout, or FP32 FFT/Gamma/stress inner iterations inside an
                      FP64 outer loop (FP64 residual, mean strain and refinement correction) */
-  int stop_rule;  /* 0: equilibrium residual eta (default); DGO uses the strain increment norm */
+  int stop_rule;  /* 0: equilibrium residual eta (default); DGO uses the strain increment norm.
+                     1: the stopping rule of Algorithms T-3D / P-3D (Sec. 5.2, 5.4): stop when
+                     sum_mu |du^(it) - du^(it-1)| < tol, the L1 norm over the modes of the unitary
+                     transform of the change of the displacement increment (the first iteration never
+                     stops).  FP64 with CD, ACD, AHC or AFB_R only (GFP_ERR_UNSUPPORTED otherwise); not
+                     with gfp_set_state resumes. */
 } gfp_scheme;
 
 typedef struct {
   int iters;              /* iterations (stress evaluations); a homogeneous cell reports 1 */
   int outer;              /* mixed precision: FP64 outer passes (0 in FP64 mode) */
-  double residual;        /* final eta */
-  double sigma_mean[6];   /* mean stress, tensor components (11,22,33,23,13,12) */
+  double residual;        /* final eta (stop_rule 1: the final increment criterion) */
+  double sigma_mean[6];   /* mean stress, tensor components (11,22,33,23,13,12); FP64 solves form it by a
+                             compensated real-space sum of C : (eps - estar) over the final strain */
   int status;             /* gfp_status of the solve */
-  double* residual_history; /* caller-owned host array of history_cap doubles, or NULL */
+  double* residual_history; /* caller-owned host array of history_cap doubles, or NULL: eta (stop_rule 1:
+                               the criterion, infinite at the first iteration) per iteration, FP64 solves */
   int history_cap;
   int launches;           /* GPU kernels this call launched (iterations are launched in chunks between
                              convergence checks, so a few after convergence run as no-ops) */

@@ -75,6 +75,52 @@ __global__ void reduce_eta_kernel(const double* __restrict__ partials, int np, S
 
 unsigned g_inject_tma_timeout = 0;
 
+// The paper's stopping rule (stop_rule 1): eta as in reduce_eta_kernel (reported), and the decision on
+// crit = scale * sum of the criterion partials, sum_k |du_it(k) - du_(it-1)(k)| over the whole spectrum
+// of the unitary transform; the first iteration has no previous increment (crit = infinity).
+__global__ void reduce_crit_kernel(const double* __restrict__ partials, const double* __restrict__ cpart, int np,
+                                   double scale, SolveState* st, double* hist, int hist_cap) {
+  if (st->done) return;
+  __shared__ double sh[2][32];
+  double s = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    s += partials[i];
+    c += cpart[i];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, off);
+    c += __shfl_down_sync(0xffffffffu, c, off);
+  }
+  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = s; sh[1][threadIdx.x >> 5] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = 0.0;
+    c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s += sh[0][w]; c += sh[1][w]; }
+    st->restart = 0;
+    const double* t = st->T0;
+    const double t0 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + 2.0 * (t[3] * t[3] + t[4] * t[4] + t[5] * t[5]);
+    const double eta = t0 > 0.0 ? sqrt(s / t0) : (s > 0.0 ? INFINITY : 0.0);
+    const int it = st->it + 1;
+    st->it = it;
+    const double prev = st->eta;
+    st->eta = eta;
+    const double crit = it == 1 ? INFINITY : scale * c;
+    st->crit = crit;
+    if (hist && it - 1 < hist_cap) hist[it - 1] = crit;
+    if (!(eta == eta) || isinf(eta) || !(crit == crit)) {
+      st->done = 3;
+    } else if (crit < st->tol) {
+      st->done = 1;
+    } else {
+      if (it > 1 && eta > prev) st->growth += 1; else st->growth = 0;
+      if (eta < st->eta_min) st->eta_min = eta;
+      if (st->growth >= 50) st->done = 3;
+      else if (it >= st->maxit) st->done = 2;
+    }
+  }
+}
+
 void launch_reduce_eta(cudaStream_t s, const double* partials, int np, SolveState* st, double* hist, int hist_cap) {
   reduce_eta_kernel<<<1, 1024, 0, s>>>(partials, np, st, hist, hist_cap);
 }
@@ -485,6 +531,8 @@ struct gfp_grid_s {
   double dgo_key[4] = {0, 0, 0, 0};  // lambda_H, mu_H, m, valid
   double* xpart = nullptr;           // per-CTA partials of the x-pass (DGO residual), n2 n3 entries
   double* estar = nullptr;           // eigenstrain [6][N] while one is set (gfp_set_eigenstrain)
+  double2* vprev = nullptr;          // stop_rule 1: previous T kt per point [3][S] (allocated on first use)
+  double* cpart64 = nullptr;         // stop_rule 1: per-CTA criterion partials (np_max)
   bool estar_on = false;
   double E_last[6] = {0, 0, 0, 0, 0, 0};  // mean strain of the last solve (displacement output)
   bool have_solution = false;
@@ -672,7 +720,7 @@ void free_grid(gfp_grid g) {
   for (int r = 0; r < 3; ++r) { cudaFree(g->tw32[r]); cudaFree(g->tabA32[r]); cudaFree(g->tabB32[r]); }
   cudaFree(g->st_in); cudaFree(g->cmean); cudaFree(g->cpart); cudaFree(g->rpart);
   for (int r = 0; r < 3; ++r) cudaFree(g->ph32[r]);
-  cudaFree(g->dgo); cudaFree(g->xpart); cudaFree(g->estar);
+  cudaFree(g->dgo); cudaFree(g->xpart); cudaFree(g->estar); cudaFree(g->vprev); cudaFree(g->cpart64);
   if (g->st_host) cudaFreeHost(g->st_host);
   if (g->st_in_host) cudaFreeHost(g->st_in_host);
   delete g;
@@ -718,17 +766,22 @@ PolarParams fp64_xparams(gfp_grid g) {
   return pp;
 }
 
-void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta) {
+void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta, const LaunchCfg* lc_override = nullptr) {
   const Dims& d = g->d;
+  const LaunchCfg& lc = lc_override ? *lc_override : g->lc64;
   g->launches += 5;
   const PolarParams pp = fp64_xparams(g);
-  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+  Passes<double>::pass_x(g->stream, lc, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
                          have_delta ? PX_DELTA : 0, nullptr, nullptr, g->st, &pp);
-  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
-  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+  Passes<double>::pass_y(g->stream, lc, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  Passes<double>::pass_z(g->stream, lc, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
                          nullptr);
-  launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, g->hist, g->hist_cap);
-  Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  if (gp.vprev)
+    reduce_crit_kernel<<<1, 1024, 0, g->stream>>>(g->partials, gp.cpart, lc.z_blocks, 1.0 / std::sqrt((double)d.N),
+                                                  g->st, g->hist, g->hist_cap);
+  else
+    launch_reduce_eta(g->stream, g->partials, lc.z_blocks, g->st, g->hist, g->hist_cap);
+  Passes<double>::pass_y(g->stream, lc, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
 }
 
 // resume: continue from the strain set by gfp_set_state; its iteration count K is taken as the
@@ -748,6 +801,21 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
   gp.half_shift = 0;
   gp.dgo = nullptr;
+  // the paper's increment rule: the previous iteration's T kt per point and the criterion partials
+  // (the TMA z-pass has no criterion: the register or generic kernel runs with these tiles)
+  LaunchCfg lc_rule = g->lc64;
+  lc_rule.z_tma = 0;
+  const bool rule1 = sc->stop_rule == 1;
+  if (rule1) {
+    if (resume) return GFP_ERR_UNSUPPORTED;
+    if (!g->vprev) GFP_CU(cudaMalloc(&g->vprev, sizeof(double2) * 3 * (size_t)g->d.S));
+    if (!g->cpart64) GFP_CU(cudaMalloc(&g->cpart64, sizeof(double) * (size_t)g->np_max));
+    GFP_CU(cudaMemsetAsync(g->vprev, 0, sizeof(double2) * 3 * (size_t)g->d.S, g->stream));
+    gp.vprev = g->vprev;
+    gp.cpart = g->cpart64;
+    gp.inv_mu = 1.0 / g->mu_h;
+    gp.c_g = (g->lam_h + g->mu_h) / (g->lam_h + 2.0 * g->mu_h);
+  }
   SolveState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.maxit = maxit;
@@ -769,13 +837,26 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
   const int budget = maxit - start_it;
   while (launched < budget) {
     const int nb = std::min(chunk, budget - launched);
-    for (int b = 0; b < nb; ++b) one_iteration64(g, gp, (launched + b) > 0 ? 1 : 0);
+    for (int b = 0; b < nb; ++b) one_iteration64(g, gp, (launched + b) > 0 ? 1 : 0, rule1 ? &lc_rule : nullptr);
     launched += nb;
     GFP_CU(cudaGetLastError());
     GFP_CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, g->stream));
     GFP_CU(cudaStreamSynchronize(g->stream));
     if (g->st_host->done) break;
     chunk = std::min(chunk * 2, 64);
+  }
+  // the mean stress of the final strain by a compensated real-space sum (the k = 0 value of the
+  // transform rounds at about 1e-16 of it)
+  if (g->st_host->done != DONE_TIMEOUT) {
+    const int mb = 512;
+    double* mpart = g->scratch;  // 8 K doubles: 12 per block
+    mean_stress64_kernel<<<mb, 256, 0, g->stream>>>(g->eps, g->lam, g->mu, g->estar_on ? g->estar : nullptr,
+                                                    g->d.N, mpart);
+    mean_stress64_final_kernel<<<1, 32, 0, g->stream>>>(mpart, mb, g->st);
+    g->launches += 2;
+    GFP_CU(cudaGetLastError());
+    GFP_CU(cudaMemcpyAsync(g->st_host->T0, g->st->T0, sizeof(double) * 6, cudaMemcpyDeviceToHost, g->stream));
+    GFP_CU(cudaStreamSynchronize(g->stream));
   }
   const SolveState& s = *g->st_host;
   g->state_iters = s.it;
@@ -787,7 +868,7 @@ int solve_fp64(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, 
     out->iters = s.it;
     out->outer = 0;
     out->launches = (int)g->launches;
-    out->residual = s.eta;
+    out->residual = rule1 ? s.crit : s.eta;
     for (int c = 0; c < 6; ++c) out->sigma_mean[c] = s.T0[c] / (double)g->d.N;
     out->status = status;
     if (out->residual_history && out->history_cap > 0) {
@@ -1430,7 +1511,10 @@ int gfp_solve(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
   if (!g || !scheme_ok(sc) || !E || !(tol >= 0.0) || maxit < 1) return GFP_ERR_ARG;
   for (int c = 0; c < 6; ++c) if (!std::isfinite(E[c])) return GFP_ERR_ARG;
   if (!g->phases) return GFP_ERR_ARG;
-  if (sc->stop_rule != 0) return GFP_ERR_UNSUPPORTED;
+  // the paper's increment rule runs in FP64 for the pairings with a single real wave vector per mode
+  if (sc->stop_rule != 0 && (sc->stop_rule != 1 || sc->prec != GFP_FP64 || sc->op == OP_F || sc->op == OP_HC ||
+                             sc->op == OP_DGO))
+    return GFP_ERR_UNSUPPORTED;
   if (g->estar_on && sc->op == OP_DGO) return GFP_ERR_UNSUPPORTED;
   for (int c = 0; c < 6; ++c) g->E_last[c] = E[c];
   g->have_solution = true;

@@ -186,7 +186,7 @@ template <typename R, int N>
 __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int ZS, int cols, int swz,
                                         const typename C<R>::T* __restrict__ ab3, const float2* vs, const Dims& d,
                                         int k10, int k2, const GammaParams<R>& gp, SolveState* __restrict__ st,
-                                        int mode, float2* __restrict__ vsrc) {
+                                        int mode, float2* __restrict__ vsrc, R* acc2 = nullptr) {
   typedef typename C<R>::T T;
   R acc = 0;
   const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
@@ -248,6 +248,10 @@ __device__ __forceinline__ R green_tile(typename C<R>::T* __restrict__ buf, int 
         else r2 *= (R)2;
       }
       acc += r2;
+      if (sizeof(R) == 8 && mode == PZ_GAMMA && acc2 && gp.vprev) {  // FP64 only (the paper's stop rule)
+        const R c = incr_point<R>(v1, v2, v3, kt1, kt2, kt3, gp, vi, d.S);
+        *acc2 += self1 ? c : (R)2 * c;
+      }
       if (mode == PZ_RESIDUAL) {
         float2 o1, o2, o3;
         o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
@@ -345,7 +349,14 @@ __global__ void __launch_bounds__(ZBound<R, N>::threads, ZBound<R, N>::blocks) p
   if (stage_v) cp_async_wait_all();
   __syncthreads();
   // Green operator, residual and T(0) per (k3, column)
-  const R acc = green_tile<R, N>(buf, ZS, cols, 0, ab3, stage_v ? vs : nullptr, d, k10, k2, gp, st, mode, vsrc);
+  R acc2 = 0;
+  const R acc = green_tile<R, N>(buf, ZS, cols, 0, ab3, stage_v ? vs : nullptr, d, k10, k2, gp, st, mode, vsrc,
+                                 &acc2);
+  if (sizeof(R) == 8 && mode == PZ_GAMMA && gp.vprev) {
+    const double s2 = block_sum((double)acc2, red);
+    if (threadIdx.x == 0) gp.cpart[blockIdx.y * gridDim.x + blockIdx.x] = s2;
+    __syncthreads();
+  }
   double accd = (double)acc;
   for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;

@@ -48,6 +48,7 @@ struct SolveState {
   double eta;      // last residual
   double eta_min;
   double T0[6];    // last unnormalised T(k = 0), tensor components
+  double crit;     // stop_rule 1: the increment criterion of the last iteration
 };
 
 // Per-axis wave-vector tables: kt_r = A_r[i_r] B_s[i_s] B_t[i_t] ((s, t) the other two axes),
@@ -63,7 +64,41 @@ struct GammaParams {
   int nyq_avg;         // average Gamma over the Hermitian partner on Nyquist planes (F, HC)
   int half_shift;      // displacement recovery: q^a = e^{i (th1 + th2 + th3)/2} i kt (AFB/R), else i kt
   const double* dgo;   // DGO: 21 Mandel entries per half-spectrum point, [21][k3][k2][P] (mode PZ_DGO)
+  // stop_rule 1 (FP64, PZ_GAMMA): the previous iteration's T kt per point, [3][k3][k2][P], updated in
+  // place, and 1 / mu_H and (lambda_H + mu_H) / (lambda_H + 2 mu_H) of G_iso; null when not in use
+  double2* vprev = nullptr;
+  double inv_mu = 0.0, c_g = 0.0;
+  double* cpart = nullptr;  // per-CTA sums of the criterion (same indexing as the residual partials)
 };
+
+// Increment criterion of the paper's stopping rule at one half-spectrum point: with q^a = a i kt and
+// q^b = b i kt (|a| = |b| = 1, the pairings CD, ACD, AHC, AFB/R), the displacement increment of
+// Algorithm T/P is (i / a) G_iso(kt) (T kt) with G_iso(kt) = [I - c kt kt / |kt|^2] / (mu_H |kt|^2), so
+// |du_it - du_(it-1)| = |G_iso(kt) (v - v_prev)| for v = T kt.  Returns that norm (unnormalised
+// transform) and stores v as the next iteration's v_prev.
+template <typename R, typename T>
+__device__ __forceinline__ R incr_point(T v1, T v2, T v3, R k1, R k2, R k3, const GammaParams<R>& gp, long long vi,
+                                        long long S) {
+  double2* pv = gp.vprev;
+  const double2 p1 = pv[vi], p2 = pv[S + vi], p3 = pv[2 * S + vi];
+  pv[vi] = make_double2((double)v1.x, (double)v1.y);
+  pv[S + vi] = make_double2((double)v2.x, (double)v2.y);
+  pv[2 * S + vi] = make_double2((double)v3.x, (double)v3.y);
+  const R s = k1 * k1 + k2 * k2 + k3 * k3;
+  if (s == (R)0) return (R)0;
+  T w1, w2, w3;
+  w1.x = v1.x - (R)p1.x; w1.y = v1.y - (R)p1.y;
+  w2.x = v2.x - (R)p2.x; w2.y = v2.y - (R)p2.y;
+  w3.x = v3.x - (R)p3.x; w3.y = v3.y - (R)p3.y;
+  const R f = (R)gp.c_g / s;
+  T kw; kw.x = k1 * w1.x + k2 * w2.x + k3 * w3.x; kw.y = k1 * w1.y + k2 * w2.y + k3 * w3.y;
+  T g1, g2, g3;
+  g1.x = w1.x - f * k1 * kw.x; g1.y = w1.y - f * k1 * kw.y;
+  g2.x = w2.x - f * k2 * kw.x; g2.y = w2.y - f * k2 * kw.y;
+  g3.x = w3.x - f * k3 * kw.x; g3.y = w3.y - f * k3 * kw.y;
+  const R n2 = g1.x * g1.x + g1.y * g1.y + g2.x * g2.x + g2.y * g2.y + g3.x * g3.x + g3.y * g3.y;
+  return sqrt(n2) * (R)gp.inv_mu / s;
+}
 
 // Discrete Green operator (Algorithm D) at one half-spectrum point: out = invN * Gamma^c t, with
 // Gamma^c stored as the upper triangle of its symmetric 6x6 Mandel matrix (basis 11,22,33,23,13,12
@@ -472,7 +507,7 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
   buf = fft_lines<false>(buf, buf2, twl, plan, LineLayout{w6, w6, 1, true});
   T* other = (buf == buf2) ? buf2 - d.n3 * w6 : buf2;
   // Green operator, residual and T(0)
-  R acc = 0;
+  R acc = 0, acc2 = 0;
   const bool ny2 = ((d.n2 & 1) == 0) && (2 * k2 == d.n2);
   const R b2 = gp.B[1][k2], a2 = gp.A[1][k2];
   for (int i = threadIdx.x; i < d.n3 * cols; i += blockDim.x) {
@@ -514,6 +549,10 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
       else r2 *= (R)2;
     }
     acc += r2;
+    if (sizeof(R) == 8 && mode == PZ_GAMMA && gp.vprev) {
+      const R c = incr_point<R>(v1, v2, v3, kt1, kt2, kt3, gp, vi, d.S);
+      acc2 += self1 ? c : (R)2 * c;
+    }
     if (mode == PZ_RESIDUAL) {
       float2 o1, o2, o3;
       o1.x = (float)v1.x; o1.y = (float)v1.y; o2.x = (float)v2.x; o2.y = (float)v2.y;
@@ -537,6 +576,11 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) buf[(z * 6 + c) * cols + cc] = o[c];
+  }
+  if (sizeof(R) == 8 && mode == PZ_GAMMA && gp.vprev) {
+    const double s2 = block_sum((double)acc2, red);
+    if (threadIdx.x == 0) gp.cpart[blockIdx.y * gridDim.x + blockIdx.x] = s2;
+    __syncthreads();
   }
   // deterministic block reduction of the residual partial (FP64 across threads)
   double accd = (double)acc;

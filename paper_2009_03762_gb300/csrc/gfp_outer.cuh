@@ -297,6 +297,63 @@ __global__ void __launch_bounds__(kResTX * kResTY) residual64_afd_kernel(const d
   }
 }
 
+// Mean stress of an FP64 strain field with compensated summation: sigma = C : (eps - estar) per voxel,
+// summed per thread and per CTA in Neumaier's form (running sum plus the accumulated rounding
+// errors), per-CTA (sum, compensation) pairs into part[12 b + 2 c], then combined in a fixed order by
+// mean_stress64_final_kernel.  The sum the transform forms at k = 0 rounds at about 1e-16 of the mean
+// stress, which is the size of the change one voxel's modulus makes in the effective stiffness of a
+// 128^3 cell; this sum keeps the rounding well below it.
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+  const double t = s + x;
+  c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) mean_stress64_kernel(const double* __restrict__ eps, const double* __restrict__ lam,
+                                                          const double* __restrict__ mu, const double* __restrict__ estar,
+                                                          long long N, double* __restrict__ part) {
+  __shared__ double sh[256][12];
+  double s[6] = {0, 0, 0, 0, 0, 0}, cp[6] = {0, 0, 0, 0, 0, 0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
+    double e[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps[c * N + v] - (estar ? estar[c * N + v] : 0.0);
+    const double m2 = 2.0 * mu[v], ltr = lam[v] * (e[0] + e[1] + e[2]);
+    neumaier_add(s[0], cp[0], m2 * e[0] + ltr);
+    neumaier_add(s[1], cp[1], m2 * e[1] + ltr);
+    neumaier_add(s[2], cp[2], m2 * e[2] + ltr);
+    neumaier_add(s[3], cp[3], m2 * e[3]);
+    neumaier_add(s[4], cp[4], m2 * e[4]);
+    neumaier_add(s[5], cp[5], m2 * e[5]);
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) { sh[threadIdx.x][2 * c] = s[c]; sh[threadIdx.x][2 * c + 1] = cp[c]; }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int c = threadIdx.x;
+    double ss = 0.0, cc = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      neumaier_add(ss, cc, sh[i][2 * c]);
+      cc += sh[i][2 * c + 1];
+    }
+    part[12 * blockIdx.x + 2 * c] = ss;
+    part[12 * blockIdx.x + 2 * c + 1] = cc;
+  }
+}
+
+// Fixed-order combination of the per-CTA pairs: st->T0[c] = sum sigma_c (the transform at k = 0).
+__global__ void mean_stress64_final_kernel(const double* __restrict__ part, int nb, SolveState* st) {
+  if (threadIdx.x < 6) {
+    const int c = threadIdx.x;
+    double ss = 0.0, cc = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      neumaier_add(ss, cc, part[12 * b + 2 * c]);
+      cc += part[12 * b + 2 * c + 1];
+    }
+    st->T0[c] = ss + cc;
+  }
+}
+
 // Sum of the per-CTA residual sums in a fixed order: st->T0 = sum sigma (the transform at k = 0) and
 // out[0] = N sum |r|^2, the spectral residual sum that reduce_eta turns into eta and the decision.
 __global__ void res64_sum_kernel(const double* __restrict__ part, int np, long long N, SolveState* st,

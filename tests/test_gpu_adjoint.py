@@ -81,7 +81,7 @@ def test_adjoint_128_lognormal_against_finite_differences():
                 vals.append(r.sigma_mean[0])
             fd = (vals[0] - vals[1]) / (2 * hstep)
             errs.append(abs(fd - grad[idx]) / abs(grad[idx]))
-    # A one-voxel perturbation moves C_1111 by ~1e-6 / N ~ 5e-13 relative, while the FFT's mean-stress sum
-    # rounds at ~1e-15 relative, so single central differences carry up to ~1e-2 relative noise; the bulk
-    # must agree to 1e-3.
-    assert np.median(errs) <= 1e-3 and max(errs) <= 1e-2, errs
+    # A one-voxel perturbation moves C_1111 by ~1e-6 / N ~ 5e-13 relative; the FP64 solve forms the mean
+    # stress by a compensated real-space sum (the k = 0 value of the transform rounds at ~4e-16, which
+    # alone would put ~1e-3 of noise on a central difference), so every voxel must agree to 1e-3.
+    assert max(errs) <= 1e-3, errs

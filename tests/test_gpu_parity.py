@@ -153,12 +153,13 @@ def test_deterministic_and_resume(gfp):
 
 def test_launch_count(gfp):
     """gfp_result.launches counts the kernels a solve launched: tol = 0 runs exactly K FP64 iterations of
-    five kernels after the strain fill; the mixed solve adds four per outer pass and two per refinement."""
+    five kernels after the strain fill, then two for the compensated mean stress; the mixed solve adds at
+    least four per outer pass and two per refinement."""
     lam, mu = M.random_field(16, 16, 16, seed=3)
     g = gfp.Grid(16, 16, 16)
     g.set_phases(lam, mu)
     r = g.solve(gfp.scheme("AFB_R", "PCD", "FP64"), [0.01, 0, 0, 0, 0, 0], 0.0, 37)
-    assert r.iters == 37 and r.launches == 1 + 5 * 37
+    assert r.iters == 37 and r.launches == 1 + 5 * 37 + 2
     rm = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), [0.01, 0, 0, 0, 0, 0], 1e-9, 5000)
     assert rm.converged and rm.outer >= 2
     assert rm.launches >= 1 + 4 * rm.outer + 2 * (rm.outer - 1) + 5 * rm.iters
