@@ -25,7 +25,7 @@ METRIC = "voxel-iterations/s"
 # DRAM bytes (read + write) per launch of the dominant kernel from ncu captures, recorded in
 # profiles/ncu_traffic.json with the hash of the kernel sources they were taken on; a record counts only
 # while the sources still hash to that value, otherwise the traffic is unknown (null).
-KERNEL_SOURCES = ("gfp_fft.cuh", "gfp_fftc.cuh", "gfp_kernels.cuh", "gfp_kimpl.cuh")
+KERNEL_SOURCES = ("gfp_fft.cuh", "gfp_fftc.cuh", "gfp_kernels.cuh", "gfp_kimpl.cuh", "gfp_tma.cuh")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
@@ -39,8 +39,7 @@ def kernel_sources_sha1():
 
 
 def ncu_traffic(kernel, n, prec, tiles):
-    """Recorded DRAM traffic per launch for this kernel and configuration, or None."""
-    zc = abs(tiles[2]) if tiles else None
+    """Recorded DRAM traffic per launch for this kernel, grid, precision and tile record, or None."""
     try:
         with open(TRAFFIC_PATH) as f:
             recs = json.load(f)["records"]
@@ -48,7 +47,8 @@ def ncu_traffic(kernel, n, prec, tiles):
         return None
     sha = kernel_sources_sha1()
     for rec in recs:
-        if (rec["kernel"], rec["n"], rec["prec"], rec["z_cols"]) == (kernel, n, prec, zc) and rec["sources_sha1"] == sha:
+        if (rec["kernel"], rec["n"], rec["prec"], list(rec["tiles"])) == (kernel, n, prec, list(tiles or [])) \
+                and rec["sources_sha1"] == sha:
             return rec["dram_read_bytes"] + rec["dram_write_bytes"]
     return None
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -356,7 +356,8 @@ def convergence_experiment(args):
     --conv-rule residual: eta < --conv-tol (ACD and AFB/R mixed precision, F FP64);
     --conv-rule increment: the paper's rule sum |du^(it) - du^(it-1)| < --conv-tol for ACD and AFB/R
     (FP64; the increment rule needs a single real wave vector per mode, so F keeps the residual rule).
-    F runs to --conv-maxit-f iterations (the paper reports it unconverged after 10^4 at high contrast)."""
+    F runs to --conv-maxit-f iterations (the paper reports it unconverged after 10^4 at high contrast), at
+    the contrasts of --conv-f-chi only."""
     import torch
     from paper_2009_03762_gb300 import gfp, microstructure as M
     n = args.n
@@ -367,13 +368,14 @@ def convergence_experiment(args):
     out = []
     g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
     inc = args.conv_rule == "increment"
-    for chi in (1e-3, 1e-2, 1e-1, 10.0, 1e2, 1e3):
+    f_chis = [float(v) for v in args.conv_f_chi.split(",")] if args.conv_f_chi else None
+    for chi in [float(v) for v in args.conv_chi.split(",")]:
         lam = 0.6 * (1.0 + f * (chi - 1.0))
         mu = lam.copy()
         refs = [("mean", None)] + ([("C_I", (0.6 * chi, 0.6 * chi))] if chi > 1 else [])
         for ref_name, ref in refs:
             g.set_phases(lam, mu, ref)
-            runs = [("F", "FP64", 0, args.conv_maxit_f)]
+            runs = [("F", "FP64", 0, args.conv_maxit_f)] if f_chis is None or chi in f_chis else []
             for op in ("ACD", "AFB_R"):
                 runs.append((op, "FP64" if inc else "MIXED", 1 if inc else 0, 20000))
             for op, prec, rule, maxit in runs:
@@ -399,10 +401,12 @@ def schemes128_experiment(args):
     from paper_2009_03762_gb300 import gfp, microstructure as M
     n = 128
     g = gfp.Grid(n, n, n, 1.0, torch.cuda.current_stream().cuda_stream)
-    for chi in (1e-3, 1e-1, 10.0, 1e3):
+    chis = [float(v) for v in args.schemes_chi.split(",")]
+    ops = args.schemes_ops.split(",")
+    for chi in chis:
         lam, mu = M.smooth_cube(n, 64, chi, width=2.0)
         g.set_phases(lam, mu)
-        for op in ("F", "CD", "ACD", "HC", "AHC", "AFB_R", "DGO"):
+        for op in ops:
             maxit = args.schemes_maxit_slow if op in ("F", "HC") else 20000
             sch = gfp.scheme(op, "PCD", "FP64", dgo_m=n // 2 if op == "DGO" else 0)
             torch.cuda.synchronize()
@@ -423,8 +427,9 @@ def schemes128_experiment(args):
 
 def batch_experiment(args):
     """Batched homogenization: random-sphere cells (n from {64, 96, 128}, volume fraction U[0.1, 0.3],
-    contrast log-uniform on [1e-2, 1e3]) x 6 Voigt loads in one graph-replayed gfp_solve_batch, mixed
-    precision to eta < 1e-8, against the same cells solved one after another (gfp_effective_stiffness).
+    contrast log-uniform on [1e-2, 1e3]) x 6 Voigt loads, mixed precision to eta < 1e-8, as one batch
+    graph (gfp_batch_create once; each gfp_batch_solve is one graph launch in which every slot loops on
+    the device), against the same cells solved one after another (gfp_effective_stiffness).
     Aggregate voxel-iterations/s = sum over cells and loads of N x inner iterations / wall time."""
     import torch
     from paper_2009_03762_gb300 import gfp, microstructure as M
@@ -443,9 +448,15 @@ def batch_experiment(args):
         grids.append(g)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    C, its, rc = gfp.solve_batch(grids, sch, tol=1e-8, maxit=args.batch_maxit)
+    batch = gfp.Batch(grids, sch)
+    t_create = time.perf_counter() - t0
+    C, its, rc = batch.solve(tol=1e-8, maxit=args.batch_maxit)  # first launch of the instantiated graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C, its, rc = batch.solve(tol=1e-8, maxit=args.batch_maxit)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    batch.close()
     vox_its = float(sum(sp["n"] ** 3 * int(its[i].sum()) for i, sp in enumerate(specs)))
     t0 = time.perf_counter()
     seq_its = 0.0
@@ -461,7 +472,10 @@ def batch_experiment(args):
     return {"experiment": "batch", "cells": len(specs), "loads": 6 * len(specs), "status": gfp.STATUS[rc],
             "sizes": {str(n): sum(1 for sp in specs if sp["n"] == n) for n in sorted(tuned)},
             "tiles": {str(k): v for k, v in tuned.items()},
-            "batch": {"seconds": t_batch, "voxel_iterations": vox_its, "voxel-iterations/s": vox_its / t_batch},
+            "batch": {"seconds": t_batch, "voxel_iterations": vox_its, "voxel-iterations/s": vox_its / t_batch,
+                      "create_seconds": t_create,
+                      "note": "second gfp_batch_solve of the handle (one graph launch); create_seconds: slot "
+                              "allocation, capture and instantiation, once per batch shape"},
             "sequential": {"seconds": t_seq, "voxel_iterations": seq_its, "voxel-iterations/s": seq_its / t_seq},
             "speedup": t_seq / t_batch, "C_eff_max_rel_diff_batch_vs_sequential": max_rel,
             "inner_iterations": {"min": int(its.min()), "max": int(its.max()), "total": int(its.sum())}}
@@ -577,8 +591,12 @@ def main():
     ap.add_argument("--conv-rule", default="residual", choices=["residual", "increment"])
     ap.add_argument("--conv-interface", default="sharp", choices=["sharp", "smooth"])
     ap.add_argument("--conv-maxit-f", type=int, default=3000)
+    ap.add_argument("--conv-chi", default="1e-3,1e-2,1e-1,10,1e2,1e3", help="contrasts of conv3d")
+    ap.add_argument("--conv-f-chi", default="", help="contrasts at which conv3d runs F (default: all)")
     ap.add_argument("--batch-count", type=int, default=32)
     ap.add_argument("--schemes-maxit-slow", type=int, default=3000, help="iteration cap of F and HC in schemes128")
+    ap.add_argument("--schemes-chi", default="1e-3,1e-1,10,1e3", help="contrasts of schemes128")
+    ap.add_argument("--schemes-ops", default="F,CD,ACD,HC,AHC,AFB_R,DGO", help="schemes of schemes128")
     ap.add_argument("--batch-maxit", type=int, default=20000)
     ap.add_argument("--oracle-n", type=int, default=128, help="grid of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

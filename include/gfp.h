@@ -33,6 +33,7 @@ extern "C" {
 #endif
 
 typedef struct gfp_grid_s* gfp_grid;
+typedef struct gfp_batch_s* gfp_batch;
 
 typedef enum {
   GFP_OK = 0,
@@ -79,6 +80,15 @@ typedef struct {
                      transform of the change of the displacement increment (the first iteration never
                      stops).  FP64 with CD, ACD, AHC or AFB_R only (GFP_ERR_UNSUPPORTED otherwise); not
                      with gfp_set_state resumes. */
+  /* Variants of the discrete Green operator (GFP_DGO only; zero selects the defaults).  Algorithm D-3D
+   * prints the weights s_j = sinc(pi j / n) and the update E_check += Gamma^c T_check; with them
+   * -Gamma^c C_H has eigenvalues of both signs and the iteration can grow (on a two-phase cube at
+   * contrast 10 it does).  The defaults are the squared weights and the polarization form
+   * E = E_bar + F+ Gamma^c F- [(C - C_H) E] (the form the footnote to Algorithm D-1D names). */
+  int dgo_power;  /* 0 or 2: weights s^2 (default); 1: the printed weights s */
+  int dgo_form;   /* 0: polarization form (default); 1: the printed stress form, E_check += Gamma^c T_check */
+  int dgo_range;  /* 0: alias range nu_r in [-m, m-1] as printed; 1: [-m, m], applied as its Hermitian part
+                     1/2 (Gamma^c(omega) + Gamma^c(-omega)) since the strain is real */
 } gfp_scheme;
 
 typedef struct {
@@ -151,13 +161,27 @@ int gfp_grad(gfp_grid g, const gfp_scheme* scheme, int I, int J, double tol, int
 /* Batched homogenization (no counterpart in the paper): the six Voigt load cases of `count` cells of
  * possibly different sizes, mixed precision only (FP32 inner iterations, FP64 residual, mean strain and
  * refinement; schemes CD, ACD, AHC, AFB_R).  Every (cell, load) pair is a slot with its own device
- * state; one CUDA graph holds a window of every running slot (32 FP32 iterations, preceded by an FP64
- * residual pass when the slot's inner solve has reached its target) as parallel branches, and the graph
- * is replayed until all slots reach eta < tol or maxit iterations.  Finished slots turn into no-ops on
- * the device, and the graph is captured again without them whenever the running slots have halved.
- * The iterates and results equal those of gfp_effective_stiffness.  C_eff_out: count x 36 (row-major Voigt per cell);
- * iters_out (may be NULL): count x 6 inner iterations per load.  The cells must have their phases set.
- * Slot buffers (about 230 bytes per voxel per load) are allocated for the call and freed at its end. */
+ * buffers and state.  The batch is one CUDA graph holding one while-node per slot: the loop body is a
+ * window of the slot's solve (an FP64 residual pass when its inner solve has reached its target, then
+ * 32 FP32 inner iterations), and its last kernel decides on the device whether the slot runs another
+ * window (outer residual still >= tol and fewer than ceil(maxit / 32) windows run).  A solve is one
+ * graph launch; slots run concurrently and a finished slot stops launching.  The iterates and results
+ * equal those of gfp_effective_stiffness.
+ *
+ * gfp_batch_create: validates the cells (phases set, no eigenstrain), allocates the slot buffers
+ *   (about 230 bytes per voxel per load, owned by the handle) and builds the graph.  The grids must
+ *   outlive the handle.  Errors: GFP_ERR_ARG, GFP_ERR_UNSUPPORTED (precision, scheme, stop rule or
+ *   eigenstrain), GFP_ERR_OOM, GFP_ERR_CUDA; *out is NULL on error.
+ * gfp_batch_solve: runs the batch from eps = E_J in every slot.  C_eff_out: count x 36 (row-major Voigt
+ *   per cell); iters_out (may be NULL): count x 6 inner iterations per load.  A grid's new phases or
+ *   tiles (gfp_set_phases, gfp_set_tiles) since the last build make it build the graph again.  Returns
+ *   GFP_ERR_NOT_CONVERGED (results still filled) when a slot ran out of windows.  Calls on one handle
+ *   must not overlap.
+ * gfp_batch_destroy: waits for the handle's work and frees it.
+ * gfp_solve_batch: create, solve and destroy in one call. */
+int gfp_batch_create(int count, gfp_grid* grids, const gfp_scheme* scheme, gfp_batch* out);
+int gfp_batch_solve(gfp_batch batch, double tol, int maxit, double* C_eff_out, int* iters_out);
+int gfp_batch_destroy(gfp_batch batch);
 int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* scheme, double tol, int maxit, double* C_eff_out,
                     int* iters_out);
 

@@ -22,8 +22,8 @@ modeling of the quasi-static mechanical behavior of inhomogeneous materials"):
   form of Sec. 5.2: the displacement coefficients u_check are corrected by G_H (T_check q^b)
   until the divergence T_check q^b vanishes (`_fdd_step`); the strain is E_bar + F^+ sym(u_check (x) q^a);
 * Algorithm D-3D's discrete Green operator Gamma^c is the alias sum of the continuous isotropic
-  Gamma_H over the wave numbers k_{nu n + omega} (Sec. 5.4), with the weights and update form of
-  the weights and update form read in `_solve_dgo` by default.
+  Gamma_H over the wave numbers k_{nu n + omega} (Sec. 5.4); `_solve_dgo` states the weights and
+  the update form it uses by default.
 
 Pins (tests/test_oracle_pins.py) cover every function here; the alias sum off the coordinate axes
 is pinned by an independent construction from C_H-orthogonal projections onto compatible strains.
@@ -288,7 +288,7 @@ def green_hat_iso(k, lam_h, mu_h):
     return (np.eye(3) - c * kk) / (mu_h * k2)[..., None, None]
 
 
-def dgo_operator(n3, n2, n1, h, lam_h, mu_h, m=None, power=1):
+def dgo_operator(n3, n2, n1, h, lam_h, mu_h, m=None, power=1, alias_range="printed"):
     """Gamma^c_omega for omega in [0,n1) x [0,n2) x [0,n3), the alias sum of Algorithm D-3D:
 
       Gamma^c_0 = 0,
@@ -299,9 +299,15 @@ def dgo_operator(n3, n2, n1, h, lam_h, mu_h, m=None, power=1):
     basis p = (11, 22, 33, 23, 13, 12) with unit entries at (i, j) and (j, i).
     m defaults to n_r / 2 on every axis (m = n/2, the paper's choice); an axis with n_r = 1
     uses m_r = 1 so that its range [-m_r, m_r - 1] contains nu_r = 0.
+    alias_range = "symmetric": nu_r runs over [-m_r, m_r] instead.  That sum is not even in omega
+    (omega -> n - omega maps the term nu to -nu - 1, outside the range at nu = m), and the increment
+    of a real strain field is the real part of its inverse transform, i.e. the operator's Hermitian
+    part; so this variant returns 1/2 (Sigma(omega) + Sigma(n - omega)), the reading the Nyquist
+    modes of the finite-difference schemes take as well.
     """
     ns = (n1, n2, n3)
     ms = tuple(max(1, nr // 2 if m is None else m) for nr in ns)
+    hi = tuple(mr + 1 if alias_range == "symmetric" else mr for mr in ms)
     shape = (n3, n2, n1)
     om = [np.arange(nr) for nr in ns]
     basis = []
@@ -314,9 +320,9 @@ def dgo_operator(n3, n2, n1, h, lam_h, mu_h, m=None, power=1):
     om_grid = [np.broadcast_to(om[0][None, None, :], shape), np.broadcast_to(om[1][None, :, None], shape),
                np.broadcast_to(om[2][:, None, None], shape)]
     zero = (om_grid[0] == 0) & (om_grid[1] == 0) & (om_grid[2] == 0)
-    for n3v in range(-ms[2], ms[2]):
-        for n2v in range(-ms[1], ms[1]):
-            for n1v in range(-ms[0], ms[0]):
+    for n3v in range(-ms[2], hi[2]):
+        for n2v in range(-ms[1], hi[1]):
+            for n1v in range(-ms[0], hi[0]):
                 nu = (n1v, n2v, n3v)
                 j = [nu[r] * ns[r] + om_grid[r] for r in range(3)]
                 w = (sinc_weight(j[0], n1) * sinc_weight(j[1], n2) * sinc_weight(j[2], n3)) ** power
@@ -332,6 +338,9 @@ def dgo_operator(n3, n2, n1, h, lam_h, mu_h, m=None, power=1):
                     GBk = np.einsum("...ij,j...->i...", G, Bk)
                     out[p][:, :, live] += w[live] * (-sym_outer(GBk, kl))
     out[:, :, :, zero] = 0.0
+    if alias_range == "symmetric":
+        i3, i2, i1 = [(-np.arange(nr)) % nr for nr in (n3, n2, n1)]
+        out = 0.5 * (out + out[..., i3, :, :][..., :, i2, :][..., :, :, i1])
     return out
 
 
@@ -373,7 +382,7 @@ def _fdd_step(u, Ebar_f, T0, lam, mu, qa, qb, G, mats):
 
 def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=None,
           stop_rule=0, dgo_m=None, dgo_table=None, max_iters_exact=None, dgo_form="polarization",
-          dgo_power=2, estar=None):
+          dgo_power=2, estar=None, dgo_range="printed"):
     """Solve the periodic cell problem with Algorithm T-3D (disc='TD'), P-3D (disc='PCD') or D-3D (DGO).
 
     lam, mu: (n3, n2, n1) voxel Lame fields (already sampled at x_i or x_i^c).
@@ -399,7 +408,7 @@ def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=
         if estar is not None:
             raise ValueError("eigenstrain is not defined for Algorithm D here")
         return _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_table, max_iters_exact,
-                          dgo_form, dgo_power)
+                          dgo_form, dgo_power, dgo_range)
     mats = [dft_matrices(nr, h, disc) for nr in (n1, n2, n3)]
     qa, qb = wave_vectors(scheme, n3, n2, n1, h)
     G = green(qa, qb, lam_h, mu_h)
@@ -434,7 +443,7 @@ def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=
 
 
 def _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_table, max_iters_exact,
-               dgo_form="polarization", dgo_power=2):
+               dgo_form="polarization", dgo_power=2, dgo_range="printed"):
     """Algorithm D-3D with the omega-indexed PCD transforms F^{c+-} (x_i^c = (i - 1/2) h).
 
     Readings of the weights and the update form:
@@ -450,10 +459,13 @@ def _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_tabl
     forms converge there; the polarization form reproduces the paper's finding that the DGO
     response is stiffer than AFB/R at high contrast.
     Residual: eta_D = ||E_new - E_old||_2 / (sqrt(N) ||E_bar||_F) (unitary transforms).
+    In both forms the iterate returned includes the increment of the last iteration: Algorithm D-3D
+    adds Delta E_check to E_check inside the loop body, before the while test.
+    dgo_range: the alias range of dgo_operator ("printed" [-m, m-1] or "symmetric" [-m, m]).
     """
     n3, n2, n1 = lam.shape
     mats = [dft_matrices(nr, h, "PCD", index="omega") for nr in (n1, n2, n3)]
-    Gc = dgo_operator(n3, n2, n1, h, lam_h, mu_h, dgo_m, dgo_power) if dgo_table is None else dgo_table
+    Gc = dgo_operator(n3, n2, n1, h, lam_h, mu_h, dgo_m, dgo_power, dgo_range) if dgo_table is None else dgo_table
     Ec = np.zeros((3, 3, n3, n2, n1), dtype=np.complex128)
     Ebar_f = Ebar[:, :, None, None, None] * np.ones((1, 1, n3, n2, n1))
     enorm = np.sqrt(np.sum(Ebar ** 2)) * np.sqrt(N)
@@ -475,8 +487,6 @@ def _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_tabl
         history.append(eta)
         converged = eta < tol
         stop = (it >= max_iters_exact) if max_iters_exact is not None else (converged or it >= maxit)
-        if stop and dgo_form == "stress":
-            break
         Ec = Ec_new
         if stop:
             eps = Ebar_f + inverse3(Ec, mats).real

@@ -220,14 +220,20 @@ __constant__ int c_mono4[3][3][3][3];  // index of the degree-4 monomial k_i k_j
 __constant__ int c_mono2[3][3];        // index of the degree-2 monomial k_a k_b
 
 // Alias sums of Gamma^c at the representative points rep_pts (o1, o2, o3) packed as o1 | o2 << 11 | o3 << 22:
-// the 21 Mandel entries of each into rep [21][F3][F2][F1] (F_r = n_r/2 + 1) at (o1, o2, o3).
+// the 21 Mandel entries of each into rep [21][F3][F2][F1] at (o1, o2, o3) (F_r = n_r/2 + 1 when the axes
+// are folded, else F1 = n1/2 + 1, F2 = n2, F3 = n3).
+// sym = 0: nu_r in [-m_r, m_r - 1] (Algorithm D-3D).  sym = 1: the Hermitian part of the sum over
+// [-m_r, m_r], i.e. 1/2 (sum over [-m, m]^3 + sum over [-m - 1, m - 1]^3) at omega (omega -> n - omega on
+// all three axes at once maps nu to -nu - 1 and k to -k, which leaves every moment unchanged), summed over
+// [-m - 1, m]^3 with the factor c(nu) = 1/2 ([all nu_r >= -m_r] + [all nu_r <= m_r - 1]).  A flip of
+// one axis alone does not map c onto itself, so the sym table is computed at every point, unfolded.  The
+// weight tables w_r cover nu_r in [lo_r, lo_r + W_r), W_r = 2 m_r (+ 2 with sym).
 __global__ void dgo_table_kernel(double* __restrict__ rep, const int* __restrict__ rep_pts, int nrep, Dims d,
-                                 const double* __restrict__ w1, const double* __restrict__ w2,
-                                 const double* __restrict__ w3, int m1, int m2, int m3, double h, double lam_h,
-                                 double mu_h) {
+                                 int F1, int F2, int F3, const double* __restrict__ w1,
+                                 const double* __restrict__ w2, const double* __restrict__ w3, int m1, int m2,
+                                 int m3, int sym, double h, double lam_h, double mu_h) {
   const double two_pi = 6.283185307179586476925;
   const double cc = (lam_h + mu_h) / (lam_h + 2.0 * mu_h);
-  const int F1 = d.n1 / 2 + 1, F2 = d.n2 / 2 + 1, F3 = d.n3 / 2 + 1;
   const long long RS = (long long)F1 * F2 * F3;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nrep; idx += gridDim.x * blockDim.x) {
     const int code = rep_pts[idx];
@@ -239,25 +245,30 @@ __global__ void dgo_table_kernel(double* __restrict__ rep, const int* __restrict
       // FP64 division is slow on this GPU: the axis scales are precomputed, each term takes one
       // reciprocal of |k|^2, and the fourth moments are formed from the six pair products
       const double f1 = two_pi / ((double)d.n1 * h), f2 = two_pi / ((double)d.n2 * h), f3 = two_pi / ((double)d.n3 * h);
-      for (int v3 = -m3; v3 < m3; ++v3) {
-        const double s3 = w3[o3 * 2 * m3 + (v3 + m3)];
+      const int lo1 = sym ? -m1 - 1 : -m1, lo2 = sym ? -m2 - 1 : -m2, lo3 = sym ? -m3 - 1 : -m3;
+      const int W1 = sym ? 2 * m1 + 2 : 2 * m1, W2 = sym ? 2 * m2 + 2 : 2 * m2, W3 = sym ? 2 * m3 + 2 : 2 * m3;
+      for (int v3 = lo3; v3 < lo3 + W3; ++v3) {
+        const double s3 = w3[o3 * W3 + (v3 - lo3)];
         if (s3 == 0.0) continue;
         const double k3 = f3 * (double)((long long)v3 * d.n3 + o3);
-        for (int v2 = -m2; v2 < m2; ++v2) {
-          const double s2 = w2[o2 * 2 * m2 + (v2 + m2)];
+        for (int v2 = lo2; v2 < lo2 + W2; ++v2) {
+          const double s2 = w2[o2 * W2 + (v2 - lo2)];
           if (s2 == 0.0) continue;
           const double k2 = f2 * (double)((long long)v2 * d.n2 + o2);
           const double s23 = s2 * s3;
           const double p22 = k2 * k2, p33 = k3 * k3, p23 = k2 * k3;
-          for (int v1 = -m1; v1 < m1; ++v1) {
-            const double s1 = w1[o1 * 2 * m1 + (v1 + m1)];
+          const bool a23 = v2 >= -m2 && v3 >= -m3, b23 = v2 <= m2 - 1 && v3 <= m3 - 1;
+          for (int v1 = lo1; v1 < lo1 + W1; ++v1) {
+            const double s1 = w1[o1 * W1 + (v1 - lo1)];
             if (s1 == 0.0) continue;
+            const double cf = sym ? 0.5 * ((a23 && v1 >= -m1 ? 1.0 : 0.0) + (b23 && v1 <= m1 - 1 ? 1.0 : 0.0)) : 1.0;
+            if (cf == 0.0) continue;
             const double k1 = f1 * (double)((long long)v1 * d.n1 + o1);
             const double p11 = k1 * k1;
             const double kk = p11 + p22 + p33;
             if (kk == 0.0) continue;
             const double inv = 1.0 / kk;
-            const double a = s1 * s23 * inv, b = a * inv;
+            const double a = cf * s1 * s23 * inv, b = a * inv;
             // pair products k_i k_j, i <= j: (11, 12, 13, 22, 23, 33)
             const double pp[6] = {p11, k1 * k2, k1 * k3, p22, p23, p33};
             S2[0] += a * p11; S2[1] += a * p22; S2[2] += a * p33;
@@ -298,14 +309,15 @@ __global__ void dgo_table_kernel(double* __restrict__ rep, const int* __restrict
   }
 }
 
-// The table at every half-spectrum point from the representatives.  Axis r folds to
+// The table at every half-spectrum point from the representatives.  With `fold`, axis r folds to
 // f_r = min(o_r, n_r - o_r): the alias sum of n_r - o_r runs over the same terms with k_r negated
-// (nu_r -> -nu_r - 1 keeps the weight), so an entry with tensor indices (i, j, a, b) takes the sign
-// s_i s_j s_a s_b, s_r = -1 on folded axes.  On a cubic grid (`cubic`: equal lengths and alias ranges)
-// the folded point is sorted, g = (f_sig(0), f_sig(1), f_sig(2)) ascending, and the isotropic Gamma_H
-// gives Gamma^c(f)_ijab = Gamma^c(g)_{pi(i) pi(j) pi(a) pi(b)} with pi the inverse of sig.
-__global__ void dgo_expand_kernel(double* __restrict__ tab, const double* __restrict__ rep, Dims d, int cubic) {
-  const int F1 = d.n1 / 2 + 1, F2 = d.n2 / 2 + 1, F3 = d.n3 / 2 + 1;
+// (nu_r -> -nu_r - 1 keeps the weight and the range [-m, m - 1]), so an entry with tensor indices
+// (i, j, a, b) takes the sign s_i s_j s_a s_b, s_r = -1 on folded axes.  On a cubic grid (`cubic`: equal
+// lengths and alias ranges) the folded point is sorted, g = (f_sig(0), f_sig(1), f_sig(2)) ascending, and
+// the isotropic Gamma_H gives Gamma^c(f)_ijab = Gamma^c(g)_{pi(i) pi(j) pi(a) pi(b)} with pi the inverse
+// of sig.  Without `fold` every point is its own representative.
+__global__ void dgo_expand_kernel(double* __restrict__ tab, const double* __restrict__ rep, Dims d, int F1, int F2,
+                                  int F3, int fold, int cubic) {
   const long long RS = (long long)F1 * F2 * F3;
   const long long npts = (long long)d.n1h * d.n2 * d.n3;
   const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
@@ -316,9 +328,9 @@ __global__ void dgo_expand_kernel(double* __restrict__ tab, const double* __rest
     const int n[3] = {d.n1, d.n2, d.n3};
     int f[3], sg[3];
     for (int r = 0; r < 3; ++r) {
-      const bool fold = o[r] > n[r] / 2;
-      f[r] = fold ? n[r] - o[r] : o[r];
-      sg[r] = fold ? -1 : 1;
+      const bool fl = fold && o[r] > n[r] / 2;
+      f[r] = fl ? n[r] - o[r] : o[r];
+      sg[r] = fl ? -1 : 1;
     }
     int pi[3] = {0, 1, 2};  // axis r of f is axis pi[r] of the representative
     int g[3] = {f[0], f[1], f[2]};
@@ -404,6 +416,41 @@ struct BatchAcc {
   int outer;  // FP64 outer passes
 };
 
+// Parameters of one batched solve, read by the slots' kernels on the device (so that one instantiated
+// graph serves any tolerance and iteration budget).
+struct BatchCtl {
+  double tol;
+  int max_windows;
+};
+
+// First kernel of a slot's window: on the slot's first window the initial state (eps = E_J for the
+// Voigt unit load J, zero FP32 correction, fresh outer and inner states); a no-op afterwards.
+__global__ void batch_init_kernel(double* __restrict__ eps, float* __restrict__ eps32, long long N, int load,
+                                  SolveState* __restrict__ st, SolveState* __restrict__ st_in, BatchAcc* acc,
+                                  double* __restrict__ cmean, const int* __restrict__ windows,
+                                  const BatchCtl* __restrict__ ctl) {
+  if (*windows != 0) return;
+  const double e = load < 3 ? 1.0 : 0.5;  // tensor component of the Voigt unit strain
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 6 * N; i += stride) {
+    eps[i] = (i / N == load) ? e : 0.0;
+    eps32[i] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    SolveState s0;
+    memset(&s0, 0, sizeof(s0));
+    s0.maxit = 1 << 30;
+    s0.tol = ctl->tol;
+    s0.eta = INFINITY;
+    s0.eta_min = INFINITY;
+    *st = s0;
+    *st_in = s0;
+    acc->inner = 0;
+    acc->outer = 0;
+    for (int c = 0; c < 6; ++c) cmean[c] = 0.0;
+  }
+}
+
 // Start of a slot's window: if its inner iterations stopped at the window cap (state 2) they continue
 // for another window and the FP64 outer pass is held (DONE_HELD makes its kernels no-ops); otherwise
 // (first window, inner target reached, inner divergence) the outer pass runs.
@@ -421,7 +468,7 @@ __global__ void batch_gate_kernel(SolveState* __restrict__ st, SolveState* __res
 // the target max(tol/2, ratio eta_64) and the reference stress norm of the outer pass; a converged
 // slot leaves its inner state done.
 __global__ void batch_arm_kernel(SolveState* __restrict__ st, SolveState* __restrict__ st_in, BatchAcc* acc,
-                                 double tol, double ratio, int window) {
+                                 const BatchCtl* __restrict__ ctl, double ratio, int window) {
   if (threadIdx.x != 0) return;
   if (st->done == DONE_HELD) {
     st->done = 0;
@@ -439,24 +486,20 @@ __global__ void batch_arm_kernel(SolveState* __restrict__ st, SolveState* __rest
   st_in->maxit = window;
   st_in->eta = INFINITY;
   st_in->eta_min = INFINITY;
-  st_in->tol = fmax(0.5 * tol, ratio * st->eta);
+  st_in->tol = fmax(0.5 * ctl->tol, ratio * st->eta);
   st_in->restart = 1;
   for (int c = 0; c < 6; ++c) st_in->T0[c] = st->T0[c];
 }
 
-// After a window: running[i] = 1 while slot i's outer state is still running, and the number of
-// running slots.
-__global__ void batch_status_kernel(SolveState* const* __restrict__ sts, int n, int* running, int* count) {
-  __shared__ int c;
-  if (threadIdx.x == 0) c = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int r = sts[i]->done == 0;
-    running[i] = r;
-    if (r) atomicAdd(&c, 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *count = c;
+// Last kernel of a slot's window: counts the window and sets the slot's loop condition, so that the
+// slot's while-node runs another window while its outer state is running and the window budget lasts.
+// The count rises by one per window, so every slot's loop ends after at most max_windows windows.
+__global__ void batch_loop_kernel(cudaGraphConditionalHandle h, const SolveState* __restrict__ st,
+                                  int* __restrict__ windows, const BatchCtl* __restrict__ ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int w = *windows + 1;
+  *windows = w;
+  cudaGraphSetConditional(h, (st->done == 0 && w < ctl->max_windows) ? 1u : 0u);
 }
 
 }  // namespace gfp
@@ -491,6 +534,7 @@ struct gfp_grid_s {
   double* mu = nullptr;
   double lam_h = 0, mu_h = 0;
   bool phases = false;
+  int phase_gen = 0;          // incremented by gfp_set_phases and gfp_set_tiles (batch graphs bake both in)
   double* eps = nullptr;
   double2* spec = nullptr;
   double2* tw64[3] = {nullptr, nullptr, nullptr};
@@ -528,7 +572,7 @@ struct gfp_grid_s {
   float2* ph32[3] = {nullptr, nullptr, nullptr};  // e^{i th_r / 2} per axis (stencil phase of AHC, AFB/R)
   // discrete Green operator table and the key it was built for
   double* dgo = nullptr;
-  double dgo_key[4] = {0, 0, 0, 0};  // lambda_H, mu_H, m, valid
+  double dgo_key[6] = {0, 0, 0, 0, 0, 0};  // lambda_H, mu_H, m, valid, weight power, symmetric range
   double* xpart = nullptr;           // per-CTA partials of the x-pass (DGO residual), n2 n3 entries
   double* estar = nullptr;           // eigenstrain [6][N] while one is set (gfp_set_eigenstrain)
   double2* vprev = nullptr;          // stop_rule 1: previous T kt per point [3][S] (allocated on first use)
@@ -1119,30 +1163,30 @@ int solve_mixed(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol,
 }
 
 // Sinc weights s_j = sinc(pi j / n) of axis r raised to `power`, for omega in [0, n) (rows) and
-// nu in [-m, m) (columns); exact zeros where j = 0 mod n, j != 0.
-void dgo_weights(int n, int m, int power, std::vector<double>& w) {
+// nu in [lo, lo + W) (columns); exact zeros where j = 0 mod n, j != 0.
+void dgo_weights(int n, int lo, int W, int power, std::vector<double>& w) {
   const double pi = 3.14159265358979323846;
-  w.assign((size_t)n * 2 * m, 0.0);
+  w.assign((size_t)n * W, 0.0);
   for (int o = 0; o < n; ++o)
-    for (int v = -m; v < m; ++v) {
+    for (int v = lo; v < lo + W; ++v) {
       const long long j = (long long)v * n + o;
       double s;
       if (j == 0) s = 1.0;
       else if (j % n == 0) s = 0.0;
       else { const double x = pi * (double)j / (double)n; s = std::sin(x) / x; }
-      w[(size_t)o * 2 * m + (v + m)] = power == 2 ? s * s : s;
+      w[(size_t)o * W + (v - lo)] = power == 2 ? s * s : s;
     }
 }
 
 std::once_flag g_mono_once;
 
-int ensure_dgo(gfp_grid g, int dgo_m) {
+int ensure_dgo(gfp_grid g, int dgo_m, int power, int sym) {
   const Dims& d = g->d;
   const int ns[3] = {g->n1, g->n2, g->n3};
   int ms[3];
   for (int r = 0; r < 3; ++r) ms[r] = std::max(1, dgo_m > 0 ? dgo_m : ns[r] / 2);
   if (g->dgo && g->dgo_key[3] == 1.0 && g->dgo_key[0] == g->lam_h && g->dgo_key[1] == g->mu_h &&
-      g->dgo_key[2] == (double)dgo_m)
+      g->dgo_key[2] == (double)dgo_m && g->dgo_key[4] == (double)power && g->dgo_key[5] == (double)sym)
     return GFP_OK;
   static int mono_err = 0;
   std::call_once(g_mono_once, [] {
@@ -1171,14 +1215,16 @@ int ensure_dgo(gfp_grid g, int dgo_m) {
   double* w[3] = {nullptr, nullptr, nullptr};
   for (int r = 0; r < 3; ++r) {
     std::vector<double> hw;
-    dgo_weights(ns[r], ms[r], 2, hw);
+    dgo_weights(ns[r], sym ? -ms[r] - 1 : -ms[r], sym ? 2 * ms[r] + 2 : 2 * ms[r], power, hw);
     GFP_CU(cudaMalloc(&w[r], sizeof(double) * hw.size()));
     GFP_CU(cudaMemcpy(w[r], hw.data(), sizeof(double) * hw.size(), cudaMemcpyHostToDevice));
   }
   GFP_CU(cudaMemsetAsync(g->dgo, 0, sizeof(double) * 21 * (size_t)d.S, g->stream));
-  // representatives: every axis folded to [0, n_r/2]; on a cubic grid also sorted ascending
-  const bool cubic = ns[0] == ns[1] && ns[1] == ns[2] && ms[0] == ms[1] && ms[1] == ms[2];
-  const int F[3] = {ns[0] / 2 + 1, ns[1] / 2 + 1, ns[2] / 2 + 1};
+  // representatives: every axis folded to [0, n_r/2] and, on a cubic grid, sorted ascending (printed
+  // range); every half-spectrum point (symmetric range, whose sum is even only in all axes at once)
+  const bool fold = !sym;
+  const bool cubic = fold && ns[0] == ns[1] && ns[1] == ns[2] && ms[0] == ms[1] && ms[1] == ms[2];
+  const int F[3] = {ns[0] / 2 + 1, fold ? ns[1] / 2 + 1 : ns[1], fold ? ns[2] / 2 + 1 : ns[2]};
   std::vector<int> pts;
   for (int o3 = 0; o3 < F[2]; ++o3)
     for (int o2 = 0; o2 < F[1]; ++o2)
@@ -1192,10 +1238,10 @@ int ensure_dgo(gfp_grid g, int dgo_m) {
   if (e == cudaSuccess) {
     const int nrep = (int)pts.size();
     dgo_table_kernel<<<std::max(1, std::min(4096, (nrep + 63) / 64)), 64, 0, g->stream>>>(
-        rep, dpts, nrep, d, w[0], w[1], w[2], ms[0], ms[1], ms[2], g->h, g->lam_h, g->mu_h);
+        rep, dpts, nrep, d, F[0], F[1], F[2], w[0], w[1], w[2], ms[0], ms[1], ms[2], sym, g->h, g->lam_h, g->mu_h);
     const long long npts = (long long)d.n1h * d.n2 * d.n3;
-    dgo_expand_kernel<<<(int)std::min<long long>(4096, (npts + 255) / 256), 256, 0, g->stream>>>(g->dgo, rep, d,
-                                                                                                  cubic ? 1 : 0);
+    dgo_expand_kernel<<<(int)std::min<long long>(4096, (npts + 255) / 256), 256, 0, g->stream>>>(
+        g->dgo, rep, d, F[0], F[1], F[2], fold ? 1 : 0, cubic ? 1 : 0);
     g->launches += 2;
     e = cudaGetLastError();
   }
@@ -1208,14 +1254,19 @@ int ensure_dgo(gfp_grid g, int dgo_m) {
   g->dgo_key[1] = g->mu_h;
   g->dgo_key[2] = (double)dgo_m;
   g->dgo_key[3] = 1.0;
+  g->dgo_key[4] = (double)power;
+  g->dgo_key[5] = (double)sym;
   return GFP_OK;
 }
 
-// Algorithm D-3D in the polarization form with s^2 weights: eps = E_bar + F+ Gamma^c F- [(C - C_H) eps];
-// iteration `it` forms eps^(it) in the x-pass of the next launch and the residual
-// ||eps^(it) - eps^(it-1)|| / (sqrt(N) ||E_bar||_F) is reduced right after it.
+// Algorithm D-3D.  Polarization form (default): eps = E_bar + F+ Gamma^c F- [(C - C_H) eps]; stress form
+// (as printed): eps += F+ Gamma^c F- [C : eps].  Iteration `it` forms eps^(it) in the x-pass of the next
+// launch, and the residual ||eps^(it) - eps^(it-1)|| / (sqrt(N) ||E_bar||_F) is reduced right after it;
+// the returned strain includes the last increment (Algorithm D-3D adds it inside the loop body).
 int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, int maxit, gfp_result* out) {
-  int rc = ensure_dgo(g, sc->dgo_m);
+  const int power = sc->dgo_power == 1 ? 1 : 2;
+  const bool stress_form = sc->dgo_form == 1;
+  int rc = ensure_dgo(g, sc->dgo_m, power, sc->dgo_range == 1 ? 1 : 0);
   if (rc) return rc;
   rc = ensure_tables(g, OP_AFB_R);  // the DGO path does not read k-tables; keep them valid
   if (rc) return rc;
@@ -1252,7 +1303,8 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
     for (int b = 0; b < nb; ++b) {
       const int j = launched + b;
       Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
-                             PX_POLAR | (j > 0 ? PX_DELTA : 0), nullptr, nullptr, g->st, &pp);
+                             (stress_form ? PX_DRES : PX_POLAR) | (j > 0 ? PX_DELTA : 0), nullptr, nullptr, g->st,
+                             &pp);
       if (j > 0) reduce_dgo_kernel<<<1, 256, 0, g->stream>>>(g->xpart, np, enorm, g->st, g->hist, g->hist_cap);
       g->launches += j > 0 ? 5 : 4;
       Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
@@ -1301,7 +1353,8 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
 
 bool scheme_ok(const gfp_scheme* sc) {
   return sc && sc->op >= 0 && sc->op <= OP_DGO && (sc->disc == GFP_TD || sc->disc == GFP_PCD) &&
-         (sc->prec == GFP_FP64 || sc->prec == GFP_MIXED);
+         (sc->prec == GFP_FP64 || sc->prec == GFP_MIXED) && sc->dgo_power >= 0 && sc->dgo_power <= 2 &&
+         (sc->dgo_form == 0 || sc->dgo_form == 1) && (sc->dgo_range == 0 || sc->dgo_range == 1);
 }
 
 }  // namespace
@@ -1503,6 +1556,7 @@ int gfp_set_phases(gfp_grid g, const double* lambda, const double* mu, int where
     g->mu_h = 0.5 * (q[2] + (-q[3]));
   }
   g->phases = true;
+  ++g->phase_gen;
   g->lam32_valid = false;
   return GFP_OK;
 }
@@ -2070,14 +2124,17 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   lc.z_tma = tiles[2] < 0 ? 1 : 0;
   finalize_cfg(d, lc);
   refresh_ztmap(g, mixed);
+  ++g->phase_gen;
   return GFP_OK;
 }
 
 }  // extern "C"
 
-// ---- batched homogenization: every (microstructure, Voigt load) pair is a slot with its own state;
-// one CUDA graph holds a window (FP64 residual pass + `window` FP32 inner iterations) for all slots as
-// parallel branches and is replayed until every slot has converged.
+// ---- batched homogenization: every (microstructure, Voigt load) pair is a slot with its own state.
+// The batch is one CUDA graph of one while-node per slot; a slot's loop body is one window (the FP64
+// residual pass when the inner solve has reached its target, then `window` FP32 inner iterations), and
+// its last kernel decides on the device whether the slot loops again.  One graph launch solves the
+// whole batch: no host round trip between windows, and a finished slot stops launching.
 namespace {
 
 struct BatchSlot {
@@ -2105,11 +2162,16 @@ void free_slot(BatchSlot& s) {
   if (s.stream) cudaStreamDestroy(s.stream);
 }
 
-void slot_window(BatchSlot& s, int op, const GammaParams<float>& gp32, double tol, int window) {
+constexpr int kBatchWindow = 32;
+
+void slot_window(BatchSlot& s, int op, const GammaParams<float>& gp32, const BatchCtl* ctl, const int* windows,
+                 int window) {
   gfp_grid g = s.g;
   const Dims& d = g->d;
   cudaStream_t st = s.stream;
   const int cvb = (int)std::min<long long>(1024, (d.N + 255) / 256);
+  batch_init_kernel<<<(int)std::min<long long>(4096, (6 * d.N + 255) / 256), 256, 0, st>>>(
+      s.eps, s.eps32, d.N, s.load, s.st, s.st_in, s.acc, s.cmean, windows, ctl);
   batch_gate_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, window);
   // the FP64 outer pass and the inner source: no-ops while the slot's outer state is held or done
   long long launches = 0;
@@ -2117,7 +2179,7 @@ void slot_window(BatchSlot& s, int op, const GammaParams<float>& gp32, double to
                s.rpart, s.partials, s.st, launches);
   outer_source32(st, s.lc32, d, op, reinterpret_cast<const float*>(s.spec), s.vsrc, g->tw32, g->plan, g->ph32, s.st,
                  launches);
-  batch_arm_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, s.acc, tol, kInnerReduction, window);
+  batch_arm_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, s.acc, ctl, kInnerReduction, window);
   float2* spec32 = reinterpret_cast<float2*>(s.spec);
   for (int k = 0; k < window; ++k) {
     Passes<float>::pass_x(st, s.lc32, spec32, s.eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, PX_DELTA,
@@ -2133,23 +2195,74 @@ void slot_window(BatchSlot& s, int op, const GammaParams<float>& gp32, double to
 
 }  // namespace
 
-extern "C" {
+struct gfp_batch_s {
+  std::vector<gfp_grid> grids;
+  std::vector<int> gens;          // the grids' phase_gen when the graph was built
+  gfp_scheme sc;
+  std::vector<BatchSlot> slots;
+  BatchCtl* ctl = nullptr;        // device
+  int* windows = nullptr;         // device, windows run per slot
+  cudaStream_t main = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
 
-int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol, int maxit, double* C_eff_out,
-                    int* iters_out) {
-  if (count < 1 || !grids || !scheme_ok(sc) || !(tol > 0.0) || maxit < 1 || !C_eff_out) return GFP_ERR_ARG;
-  if (sc->prec != GFP_MIXED || sc->op == OP_F || sc->op == OP_HC || sc->op == OP_DGO || sc->stop_rule != 0)
-    return GFP_ERR_UNSUPPORTED;
-  for (int i = 0; i < count; ++i)
-    if (!grids[i] || !grids[i]->phases) return GFP_ERR_ARG;
-  for (int i = 0; i < count; ++i)
-    if (grids[i]->estar_on) return GFP_ERR_UNSUPPORTED;
-  // shared per-grid data: FP32 Lame fields, tables, twiddles
+namespace {
+
+void batch_free_graph(gfp_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+void batch_free(gfp_batch b) {
+  batch_free_graph(b);
+  if (b->main) cudaStreamDestroy(b->main);
+  cudaFree(b->ctl);
+  cudaFree(b->windows);
+  for (auto& s : b->slots) free_slot(s);
+  delete b;
+}
+
+// The batch graph: one while-node per slot, its body captured from the slot's stream.
+cudaError_t batch_build_graph(gfp_batch b) {
+  batch_free_graph(b);
+  cudaError_t e = cudaGraphCreate(&b->graph, 0);
+  for (size_t i = 0; i < b->slots.size() && e == cudaSuccess; ++i) {
+    BatchSlot& s = b->slots[i];
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    const GammaParams<float> gp32 = gamma_params<float>(s.g, b->sc.op, s.g->tabA32, s.g->tabB32);
+    slot_window(s, b->sc.op, gp32, b->ctl, b->windows + i, kBatchWindow);
+    batch_loop_kernel<<<1, 32, 0, s.stream>>>(h, s.st, b->windows + i, b->ctl);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(s.stream, &captured);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  for (size_t i = 0; i < b->grids.size(); ++i) b->gens[i] = b->grids[i]->phase_gen;
+  return e;
+}
+
+// FP32 Lame fields, tables and twiddles of the batch's grids (shared by the grid's six slots).
+int batch_prepare_grids(gfp_grid* grids, int count, int op) {
   for (int i = 0; i < count; ++i) {
     gfp_grid g = grids[i];
     int rc = ensure_mixed(g);
     if (rc) return rc;
-    rc = ensure_tables(g, sc->op);
+    rc = ensure_tables(g, op);
     if (rc) return rc;
     const int cvb = (int)std::min<long long>(1024, (g->d.N + 255) / 256);
     if (!g->lam32_valid) {
@@ -2159,16 +2272,36 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
     }
     GFP_CU(cudaStreamSynchronize(g->stream));
   }
-  const int window = 32;
+  return GFP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gfp_batch_create(int count, gfp_grid* grids, const gfp_scheme* sc, gfp_batch* out) {
+  if (!out) return GFP_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || !grids || !scheme_ok(sc)) return GFP_ERR_ARG;
+  if (sc->prec != GFP_MIXED || sc->op == OP_F || sc->op == OP_HC || sc->op == OP_DGO || sc->stop_rule != 0)
+    return GFP_ERR_UNSUPPORTED;
+  for (int i = 0; i < count; ++i)
+    if (!grids[i] || !grids[i]->phases) return GFP_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (grids[i]->estar_on) return GFP_ERR_UNSUPPORTED;
+  int rc = batch_prepare_grids(grids, count, sc->op);
+  if (rc) return rc;
+  gfp_batch b = new gfp_batch_s();
+  b->grids.assign(grids, grids + count);
+  b->gens.assign(count, 0);
+  b->sc = *sc;
   const int nslots = count * 6;
-  std::vector<BatchSlot> slots(nslots);
-  std::vector<SolveState*> st_ptrs(nslots);
-  int rc = GFP_OK;
+  b->slots.resize(nslots);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count && e == cudaSuccess; ++i)
     for (int J = 0; J < 6; ++J) {
-      BatchSlot& s = slots[i * 6 + J];
+      BatchSlot& s = b->slots[i * 6 + J];
       gfp_grid g = grids[i];
       const Dims& d = g->d;
       s.g = g;
@@ -2190,116 +2323,62 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
       s.lc32 = g->lc32;
       s.lc64.ztmap = encode_ztmap(&s.zm64, s.spec, d, s.lc64.z_cols, 8) ? &s.zm64 : nullptr;
       s.lc32.ztmap = encode_ztmap(&s.zm32, s.spec, d, s.lc32.z_cols, 4) ? &s.zm32 : nullptr;
-      st_ptrs[i * 6 + J] = s.st;
     }
-  int* d_count = nullptr;
-  int* d_running = nullptr;
-  SolveState** d_sts = nullptr;
-  cudaStream_t main = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&d_running, sizeof(int) * nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&d_sts, sizeof(SolveState*) * nslots);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(d_sts, st_ptrs.data(), sizeof(SolveState*) * nslots, cudaMemcpyHostToDevice);
-  // initial state of every slot: eps = E_J, zero correction, fresh outer and inner states
-  if (e == cudaSuccess) {
-    for (auto& s : slots) {
+  A((void**)&b->ctl, sizeof(BatchCtl));
+  A((void**)&b->windows, sizeof(int) * nslots);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = batch_build_graph(b);
+  if (e != cudaSuccess) {
+    note_error(e, __LINE__);
+    batch_free(b);
+    return cuda_status(e);
+  }
+  *out = b;
+  return GFP_OK;
+}
+
+int gfp_batch_solve(gfp_batch b, double tol, int maxit, double* C_eff_out, int* iters_out) {
+  if (!b || !(tol > 0.0) || maxit < 1 || !C_eff_out) return GFP_ERR_ARG;
+  const int count = (int)b->grids.size();
+  const int nslots = (int)b->slots.size();
+  int rc = batch_prepare_grids(b->grids.data(), count, b->sc.op);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  // phases or tiles changed since the graph was built: its kernels hold the old reference medium and
+  // launch shapes, so build it again
+  bool stale = false;
+  for (int i = 0; i < count; ++i) stale = stale || b->gens[i] != b->grids[i]->phase_gen;
+  if (stale) {
+    for (auto& s : b->slots) {
+      s.lc64 = s.g->lc64;
+      s.lc32 = s.g->lc32;
       const Dims& d = s.g->d;
-      double E[6] = {0, 0, 0, 0, 0, 0};
-      E[s.load] = s.load < 3 ? 1.0 : 0.5;
-      fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, s.stream>>>(
-          s.eps, d.N, E[0], E[1], E[2], E[3], E[4], E[5]);
-      cudaMemsetAsync(s.eps32, 0, sizeof(float) * 6 * d.N, s.stream);
-      cudaMemsetAsync(s.cmean, 0, sizeof(double) * 6, s.stream);
-      cudaMemsetAsync(s.acc, 0, sizeof(BatchAcc), s.stream);
-      SolveState s0;
-      std::memset(&s0, 0, sizeof(s0));
-      s0.maxit = 1 << 30;
-      s0.tol = tol;
-      s0.eta = INFINITY;
-      s0.eta_min = INFINITY;
-      cudaMemcpy(s.st, &s0, sizeof(s0), cudaMemcpyHostToDevice);
-      cudaMemcpy(s.st_in, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+      s.lc64.ztmap = encode_ztmap(&s.zm64, s.spec, d, s.lc64.z_cols, 8) ? &s.zm64 : nullptr;
+      s.lc32.ztmap = encode_ztmap(&s.zm32, s.spec, d, s.lc32.z_cols, 4) ? &s.zm32 : nullptr;
     }
-    e = cudaDeviceSynchronize();
+    e = batch_build_graph(b);
   }
-  // one window of every running slot as parallel branches of one graph; the graph is captured again
-  // without the finished slots whenever the running ones have halved (finished slots would otherwise
-  // keep costing a launch per kernel and window)
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> joins(nslots, nullptr);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-  for (int i = 0; i < nslots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
-  auto capture = [&](const std::vector<int>& active) {
-    if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
-    if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return;
-    cudaEventRecord(fork, main);
-    for (int i : active) {
-      BatchSlot& s = slots[i];
-      cudaStreamWaitEvent(s.stream, fork, 0);
-      const GammaParams<float> gp32 = gamma_params<float>(s.g, sc->op, s.g->tabA32, s.g->tabB32);
-      slot_window(s, sc->op, gp32, tol, window);
-      cudaEventRecord(joins[i], s.stream);
-      cudaStreamWaitEvent(main, joins[i], 0);
-    }
-    batch_status_kernel<<<1, 256, 0, main>>>(d_sts, nslots, d_running, d_count);
-    e = cudaStreamEndCapture(main, &graph);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  };
-  std::vector<int> active(nslots);
-  for (int i = 0; i < nslots; ++i) active[i] = i;
-  capture(active);
-  // replay until every slot has converged (or the iteration budget is spent)
-  int windows = 0;
-  const int max_windows = std::max(1, (maxit + window - 1) / window);
-  std::vector<int> running(nslots);
-  while (e == cudaSuccess && windows < max_windows) {
-    e = cudaGraphLaunch(exec, main);
-    ++windows;
-    int count = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, main);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(main);
-    if (e != cudaSuccess || count == 0) break;
-    if (2 * count <= (int)active.size()) {
-      e = cudaMemcpy(running.data(), d_running, sizeof(int) * nslots, cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) break;
-      active.clear();
-      for (int i = 0; i < nslots; ++i)
-        if (running[i]) active.push_back(i);
-      capture(active);
-    }
-  }
-  if (fork) cudaEventDestroy(fork);
-  for (auto ev : joins) if (ev) cudaEventDestroy(ev);
-  // slots still running after the budget: the last outer pass holds their best FP64 state
+  const BatchCtl ctl{tol, std::max(1, (maxit + kBatchWindow - 1) / kBatchWindow)};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, b->main);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->windows, 0, sizeof(int) * nslots, b->main);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->main);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->main);
+  rc = GFP_OK;
   if (e == cudaSuccess) {
-    int all_done = 1;
-    for (int i = 0; i < nslots; ++i) {
-      SolveState h;
-      e = cudaMemcpy(&h, slots[i].st, sizeof(h), cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) break;
-      if (h.done == 0) all_done = 0;
-    }
-    if (e == cudaSuccess && !all_done) rc = GFP_ERR_NOT_CONVERGED;
-  }
-  if (e == cudaSuccess) {
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
       for (int J = 0; J < 6; ++J) {
-        BatchSlot& s = slots[i * 6 + J];
+        BatchSlot& s = b->slots[i * 6 + J];
         SolveState so, si;
         BatchAcc acc;
-        cudaMemcpy(&so, s.st, sizeof(so), cudaMemcpyDeviceToHost);
-        cudaMemcpy(&si, s.st_in, sizeof(si), cudaMemcpyDeviceToHost);
-        e = cudaMemcpy(&acc, s.acc, sizeof(acc), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(&so, s.st, sizeof(so), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&si, s.st_in, sizeof(si), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&acc, s.acc, sizeof(acc), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) break;
         for (int I = 0; I < 6; ++I) C_eff_out[(size_t)i * 36 + I * 6 + J] = so.T0[I] / (double)s.g->d.N;
         if (iters_out) iters_out[i * 6 + J] = acc.inner + (so.done ? 0 : si.it);
-        if (so.done == 3 && rc == GFP_OK) rc = GFP_ERR_DIVERGED;
+        // slots still running after the budget: the last outer pass holds their best FP64 state
+        if (so.done == 0 && rc == GFP_OK) rc = GFP_ERR_NOT_CONVERGED;
+        if (so.done == 3 && (rc == GFP_OK || rc == GFP_ERR_NOT_CONVERGED)) rc = GFP_ERR_DIVERGED;
         if (so.done == DONE_TIMEOUT) rc = GFP_ERR_DEVICE_TIMEOUT;
       }
   }
@@ -2307,13 +2386,24 @@ int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol
     note_error(e, __LINE__);
     rc = cuda_status(e);
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (main) cudaStreamDestroy(main);
-  cudaFree(d_count);
-  cudaFree(d_running);
-  cudaFree(d_sts);
-  for (auto& s : slots) free_slot(s);
+  return rc;
+}
+
+int gfp_batch_destroy(gfp_batch b) {
+  if (!b) return GFP_ERR_ARG;
+  cudaStreamSynchronize(b->main);
+  batch_free(b);
+  return GFP_OK;
+}
+
+int gfp_solve_batch(int count, gfp_grid* grids, const gfp_scheme* sc, double tol, int maxit, double* C_eff_out,
+                    int* iters_out) {
+  if (!(tol > 0.0) || maxit < 1 || !C_eff_out) return GFP_ERR_ARG;
+  gfp_batch b = nullptr;
+  int rc = gfp_batch_create(count, grids, sc, &b);
+  if (rc) return rc;
+  rc = gfp_batch_solve(b, tol, maxit, C_eff_out, iters_out);
+  gfp_batch_destroy(b);
   return rc;
 }
 

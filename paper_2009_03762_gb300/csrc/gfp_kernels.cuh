@@ -201,7 +201,10 @@ __device__ __forceinline__ R tk_norm2(const T t[6], R k1, R k2, R k3) {
 // PX_STRAIN: transform the strain fluctuation eps - E (pp.E) instead of the stress (no state update).
 // PX_OUTPUT (with PX_DELTA): write the inverse transform of components 0-2 to `eps`, here a [3][N]
 // output array, and stop (displacement output).
-enum { PX_DELTA = 1, PX_ZERO = 2, PX_POLAR = 4, PX_STRAIN = 8, PX_OUTPUT = 16 };
+// PX_DRES (FP64, with PX_DELTA): accumulate ||increment||_F^2 per CTA into partials[blockIdx.x] as
+// PX_POLAR does, with the plain update eps += increment and the stress C : eps (the stress form of
+// Algorithm D).
+enum { PX_DELTA = 1, PX_ZERO = 2, PX_POLAR = 4, PX_STRAIN = 8, PX_OUTPUT = 16, PX_DRES = 32 };
 
 // Polarization form of the discrete-Green-operator iteration (Algorithm D with the polarization of
 // Eloh2019): with PX_POLAR the x-pass forms eps = E_bar + inverse transform (instead of adding it),
@@ -237,6 +240,15 @@ __device__ __forceinline__ double polar_update(R e[6], const R d[6], const Polar
     s += (c < 3 ? 1.0 : 2.0) * df * df;
     e[c] = en;
   }
+  return s;
+}
+
+// Squared Frobenius norm of a strain increment (shear components count twice).
+template <typename R>
+__device__ __forceinline__ double incr_norm2(const R d[6]) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s += (c < 3 ? 1.0 : 2.0) * (double)d[c] * (double)d[c];
   return s;
 }
 
@@ -313,6 +325,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
     for (int c = 0; c < 6; ++c) cm[c] = corr_mean[c];
   }
   const bool polar = (flags & PX_POLAR) != 0;
+  const bool dres = sizeof(R) == 8 && (flags & PX_DRES) != 0;
   double dacc = 0.0;
   // state update, sigma = C : eps, repack sigma pairs for the forward transform
   for (int i = threadIdx.x; i < lines * n1; i += blockDim.x) {
@@ -343,6 +356,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
       }
       if (polar) dacc += polar_update<R>(e, dd, pp);
       else {
+        if (dres) dacc += incr_norm2<R>(dd);
 #pragma unroll
         for (int c = 0; c < 6; ++c) e[c] += dd[c];
       }
@@ -371,7 +385,7 @@ __global__ void pass_x_kernel(typename C<R>::T* __restrict__ spec, R* __restrict
     for (int p = 0; p < 3; ++p) buf[(p * lines + l) * n1 + x] = zz[p];
   }
   if (outmode) return;
-  if (polar && have_delta) {
+  if ((polar || dres) && have_delta) {
     const double sum = block_sum(dacc, red);
     if (threadIdx.x == 0) pp.partials[blockIdx.x] = sum;
   }

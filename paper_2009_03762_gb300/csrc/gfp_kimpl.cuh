@@ -77,7 +77,7 @@ inline void launch_x_c(cudaStream_t s, int want_lines, int async, typename C<R>:
                        const R* mu, const typename C<R>::T* tw, const Dims& d, int flags, const float* corr,
                        const double* corr_mean, const PolarParams& pp, const SolveState* st) {
   typedef typename C<R>::T T;
-  if (async && !(flags & (PX_POLAR | PX_STRAIN | PX_OUTPUT)) && !pp.estar) {
+  if (async && !(flags & (PX_POLAR | PX_STRAIN | PX_OUTPUT | PX_DRES)) && !pp.estar) {
     int lines = want_lines > 0 ? want_lines : 2;
     lines = std::min(lines, 512 / (3 * CPlan<N>::T));
     while (lines > 1 && xa_smem_bytes<R, N>(lines) > 200 * 1024) --lines;

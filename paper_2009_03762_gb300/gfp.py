@@ -22,7 +22,8 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSUPPORTED_SIZE", -3: "ERR_OOM", -4:
 
 class Scheme(ctypes.Structure):
     _fields_ = [("disc", ctypes.c_int), ("op", ctypes.c_int), ("dgo_m", ctypes.c_int), ("prec", ctypes.c_int),
-                ("stop_rule", ctypes.c_int)]
+                ("stop_rule", ctypes.c_int), ("dgo_power", ctypes.c_int), ("dgo_form", ctypes.c_int),
+                ("dgo_range", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -47,7 +48,7 @@ EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
            "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
            "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain", "gfp_get_displacement",
-           "gfp_measure_fma_peak")
+           "gfp_measure_fma_peak", "gfp_batch_create", "gfp_batch_solve", "gfp_batch_destroy")
 
 
 def lib():
@@ -76,6 +77,9 @@ def lib():
                                      ctypes.POINTER(_Result), vp]
     L.gfp_tune.argtypes = [vp, ctypes.POINTER(Scheme), ip, vp]
     L.gfp_solve_batch.argtypes = [ip, vp, ctypes.POINTER(Scheme), dp, ip, vp, vp]
+    L.gfp_batch_create.argtypes = [ip, vp, ctypes.POINTER(Scheme), ctypes.POINTER(vp)]
+    L.gfp_batch_solve.argtypes = [vp, dp, ip, vp, vp]
+    L.gfp_batch_destroy.argtypes = [vp]
     L.gfp_set_fault_injection.argtypes = [ip, ip]
     L.gfp_measure_fma_peak.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
@@ -104,9 +108,12 @@ def _gpu_name():
         return "gpu"
 
 
-def scheme(op="AFB_R", disc="TD", prec="FP64", dgo_m=0, stop_rule=0):
+def scheme(op="AFB_R", disc="TD", prec="FP64", dgo_m=0, stop_rule=0, dgo_power=2, dgo_form="polarization",
+           dgo_range="printed"):
+    """gfp_scheme; the dgo_* fields select the discrete-Green-operator variants (GFP_DGO only)."""
     return Scheme(TD if disc == "TD" else PCD, OPS[op], int(dgo_m), FP64 if prec == "FP64" else MIXED,
-                  int(stop_rule))
+                  int(stop_rule), int(dgo_power), 1 if dgo_form == "stress" else 0,
+                  1 if dgo_range == "symmetric" else 0)
 
 
 def _ptr_where(a):
@@ -309,8 +316,42 @@ def solve(lam, mu, op="AFB_R", E=(0.01, 0, 0, 0, 0, 0), tol=1e-8, maxit=1000, di
         g.close()
 
 
+class Batch:
+    """A batch of cells (Grid objects with phases set) x 6 Voigt loads held as one CUDA graph
+    (gfp_batch_create): slot buffers are allocated once, and each solve() is one graph launch."""
+
+    def __init__(self, grids, sch):
+        self.grids = list(grids)  # the handle uses the grids: keep them alive
+        self.count = len(self.grids)
+        handles = (ctypes.c_void_p * self.count)(*[g._h.value for g in self.grids])
+        self._h = ctypes.c_void_p()
+        _check(lib().gfp_batch_create(self.count, ctypes.cast(handles, ctypes.c_void_p), ctypes.byref(sch),
+                                      ctypes.byref(self._h)), "gfp_batch_create")
+
+    def solve(self, tol=1e-8, maxit=5000):
+        """Returns (C_eff [count, 6, 6], inner iterations [count, 6], status)."""
+        C = np.zeros((self.count, 36))
+        its = np.zeros((self.count, 6), dtype=np.int32)
+        rc = lib().gfp_batch_solve(self._h, float(tol), int(maxit), C.ctypes.data_as(ctypes.c_void_p),
+                                   its.ctypes.data_as(ctypes.c_void_p))
+        _check(rc, "gfp_batch_solve", ok=(0, -4))
+        return C.reshape(self.count, 6, 6), its, rc
+
+    def close(self):
+        if self._h:
+            lib().gfp_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def solve_batch(grids, sch, tol=1e-8, maxit=5000):
-    """Effective stiffness of several cells (Grid objects with phases set) in one graph-replayed batch.
+    """Effective stiffness of several cells (Grid objects with phases set) in one batch: one graph
+    launch in which every (cell, load) slot loops on the device until it converges (gfp_solve_batch).
 
     Returns (C_eff [count, 6, 6], inner iterations [count, 6], status).
     """

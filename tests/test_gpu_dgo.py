@@ -70,3 +70,38 @@ def test_dgo_fixed_iterations_register_fft_size(gfp):
     ref = O.solve(lam, mu, "DGO", E, max_iters_exact=4, dgo_m=2)
     assert r.iters == 4
     assert _rel(eps, ref.eps) <= REL
+
+
+VARIANTS = [(p, f, r) for p in (1, 2) for f in ("polarization", "stress") for r in ("printed", "symmetric")]
+
+
+@pytest.mark.parametrize("power,form,rng", VARIANTS)
+def test_dgo_variants_fixed_iterations(gfp, power, form, rng):
+    """Every weight / update-form / alias-range variant of the discrete Green operator, 40 iterations on a
+    non-cubic random field element by element (the printed s weights grow there in the stress form; the
+    iterates still agree), with the residual history."""
+    n1, n2, n3 = 8, 6, 4
+    lam, mu = M.random_field(n1, n2, n3, seed=5)
+    E = [0.01, 0.0, 0.0, 0.0, 0.003, 0.0]
+    g = gfp.Grid(n1, n2, n3)
+    g.set_phases(lam, mu)
+    sch = gfp.scheme("DGO", "PCD", dgo_power=power, dgo_form=form, dgo_range=rng)
+    r = g.solve(sch, E, 0.0, 40, history=True)
+    ref = O.solve(lam, mu, "DGO", E, max_iters_exact=40, dgo_form=form, dgo_power=power, dgo_range=rng)
+    assert r.iters == 40 == ref.iters
+    assert _rel(g.strain(), ref.eps) <= REL
+    np.testing.assert_allclose(r.history, ref.history, rtol=1e-8)
+
+
+@pytest.mark.parametrize("power,rng", [(1, "printed"), (1, "symmetric"), (2, "symmetric")])
+def test_dgo_variants_converged_iteration_count(gfp, power, rng):
+    """Polarization-form variants that converge on a 6^3 random field: the same iteration count to 1e-10."""
+    lam, mu = M.random_field(6, 6, 6, seed=3)
+    E = [0.01, 0.0, 0.0, 0.0, 0.003, 0.0]
+    g = gfp.Grid(6, 6, 6)
+    g.set_phases(lam, mu)
+    r = g.solve(gfp.scheme("DGO", "PCD", dgo_power=power, dgo_range=rng), E, 1e-10, 1000)
+    ref = O.solve(lam, mu, "DGO", E, tol=1e-10, maxit=1000, dgo_power=power, dgo_range=rng)
+    assert r.converged and ref.converged and r.iters == ref.iters
+    assert _rel(g.strain(), ref.eps) <= REL
+    assert _rel(r.sigma_mean, ref.sigma_mean) <= REL

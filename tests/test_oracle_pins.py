@@ -666,6 +666,80 @@ def test_dgo_generic_omega_equals_projection_sum():
         np.testing.assert_allclose(_dgo_matrix(G, *om), ref, atol=1e-12)
 
 
+def _axis_alias_sum_sym(n, w, power):
+    """S+(omega) = sum_{nu=-m}^{m} sinc^p((nu n + omega)/n), m = n/2: the symmetric alias range."""
+    m = max(1, n // 2)
+    return sum(np.sinc((nu * n + w) / n) ** power for nu in range(-m, m + 1))
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_dgo_symmetric_range_1d_closed_form(power):
+    """1D, alias range [-m, m]: Gamma_H(k) = -1/C_H for every k, so the Hermitian part of the alias sum is
+    Gamma^c_omega = -(S+(omega) + S+(n - omega)) / (2 C_H); Gamma^c_0 = 0."""
+    n = 8
+    lam_h, mu_h = 0.0, 2.0
+    G = O.dgo_operator(1, 1, n, 1.0, lam_h, mu_h, power=power, alias_range="symmetric")
+    g11 = G[0, 0, 0, 0, 0, :]
+    ref = [-(_axis_alias_sum_sym(n, w, power) + _axis_alias_sum_sym(n, n - w, power)) / (2.0 * (lam_h + 2 * mu_h))
+           for w in range(1, n)]
+    np.testing.assert_allclose(g11[1:], ref, atol=1e-14)
+    assert g11[0] == 0.0
+    # the printed range differs from it by boundary terms
+    Gp = O.dgo_operator(1, 1, n, 1.0, lam_h, mu_h, power=power)
+    assert np.abs(Gp[0, 0, 0, 0, 0, 1:] - g11[1:]).max() > 1e-3
+
+
+def test_dgo_symmetric_range_even_trace_eigenvalues():
+    """3D, 4 x 6 x 8, s^2 weights, alias range [-m, m] in its Hermitian part: Gamma^c(n - omega) = Gamma^c(omega);
+    -Gamma^c C_H is half the sum of two positive combinations of rank-3 projections, so its trace is
+    3/2 (prod_r S+_r(omega_r) + prod_r S+_r(n_r - omega_r)) and its eigenvalues lie in [0, 1]."""
+    n1, n2, n3 = 4, 6, 8
+    lam_h, mu_h = 1.3, 0.6
+    G = O.dgo_operator(n3, n2, n1, 1.0, lam_h, mu_h, power=2, alias_range="symmetric")
+    idx = [(-np.arange(n)) % n for n in (n3, n2, n1)]
+    np.testing.assert_allclose(G, G[..., idx[0], :, :][..., :, idx[1], :][..., :, :, idx[2]], atol=1e-13)
+    C = _voigt_stiffness(lam_h, mu_h)
+    for w3, w2, w1 in itertools.product(range(n3), range(n2), range(n1)):
+        if w1 == w2 == w3 == 0:
+            continue
+        A = -_dgo_matrix(G, w1, w2, w3) @ C
+        Sp = _axis_alias_sum_sym(n1, w1, 2) * _axis_alias_sum_sym(n2, w2, 2) * _axis_alias_sum_sym(n3, w3, 2)
+        Sm = (_axis_alias_sum_sym(n1, (n1 - w1) % n1, 2) * _axis_alias_sum_sym(n2, (n2 - w2) % n2, 2)
+              * _axis_alias_sum_sym(n3, (n3 - w3) % n3, 2))
+        assert abs(np.trace(A) - 1.5 * (Sp + Sm)) < 1e-12
+        ev = np.linalg.eigvals(A).real
+        assert ev.min() > -1e-12 and ev.max() < 1.0 + 1e-12
+
+
+def test_dgo_alias_ranges_agree_as_m_grows():
+    """The two alias ranges differ by the terms nu = m and nu = -m - 1, of size sinc^2 ~ 1/(pi m)^2: in 1D the
+    difference falls by about 16 when m grows by 4 (s^2 weights).  Both sums tend to the full series, 1; what the
+    truncation leaves out is at most sum_{|nu| > m} 1/(pi (nu -+ 1/2))^2 < 2/(pi^2 m)."""
+    n = 6
+    d = []
+    for m in (2, 8, 32):
+        Gp = O.dgo_operator(1, 1, n, 1.0, 0.0, 0.5, m=m, power=2)[0, 0, 0, 0, 0, 1:]
+        Gs = O.dgo_operator(1, 1, n, 1.0, 0.0, 0.5, m=m, power=2, alias_range="symmetric")[0, 0, 0, 0, 0, 1:]
+        d.append(np.abs(Gp - Gs).max())
+        assert np.all(-Gs <= 1.0 + 1e-12) and np.all(-Gs >= 1.0 - 2.0 / (np.pi ** 2 * m))
+    assert d[1] < d[0] / 8 and d[2] < d[1] / 8
+
+
+@pytest.mark.parametrize("rng", ["printed", "symmetric"])
+def test_dgo_stress_form_1d_reaches_exact_solution(rng):
+    """1D, printed stress form E_check += Gamma^c T_check with s^2 weights: at its fixed point
+    S(omega) F(C E)(omega) = 0 with S > 0 at every omega != 0, so the stress C E is uniform and
+    E_i = E_bar / (C_i <1/C>) (the 1D matrix-inclusion solution of Sec. 2)."""
+    n = 10
+    rng_ = np.random.default_rng(6)
+    C = np.exp(rng_.uniform(np.log(1.0), np.log(3.0), n))
+    lam = np.zeros((1, 1, n))
+    mu = (0.5 * C).reshape(1, 1, n)
+    r = O.solve(lam, mu, "DGO", [1.0, 0, 0, 0, 0, 0], tol=1e-13, maxit=5000, dgo_form="stress", dgo_range=rng)
+    assert r.converged
+    np.testing.assert_allclose(r.eps[0, 0, 0], 1.0 / (C * np.mean(1.0 / C)), rtol=1e-11)
+
+
 def _permute_sym(E6, perm):
     """Tensor components of E'_ij = E_{perm[i] perm[j]}."""
     T = O.voigt_to_tensor(np.asarray(E6, np.float64))
