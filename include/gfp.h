@@ -198,7 +198,11 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* scheme, int iters, double pass
 
 /* Autotuner (no counterpart in the paper): times candidate tile shapes of each pass on this grid for
  * the scheme's precision -- lines per CTA of the register-FFT x-pass, k1 columns per CTA of the y and
- * z passes, and whether the z-pass loads its tiles with TMA -- and keeps the fastest.  tiles_out (may be
+ * z passes, and whether the z-pass loads its tiles with TMA -- and keeps the fastest; then, on every
+ * axis whose length has no compile-time register-FFT plan (lengths other than 32, 64, 96, 128, 192,
+ * 256, 512), it times candidate radix schedules of the shared-memory Stockham pass (the power of two
+ * as radix-16, -8 or -4 stages, the radix-3 stages first or last) and keeps the fastest
+ * (gfp_get_plans reads them).  tiles_out (may be
  * NULL) receives {x lines, y columns, z columns}, the x entry negated when the x-pass stages its loads
  * with cp.async and the z entry negated when the TMA z-pass is chosen.
  * The strain state is modified; call before a solve. */
@@ -207,6 +211,15 @@ int gfp_tune(gfp_grid g, const gfp_scheme* scheme, int iters, int tiles_out[3]);
 /* Apply tile shapes for one precision (GFP_FP64 or GFP_MIXED), e.g. read from a tuning cache, in the
  * format gfp_tune returns; invalid shapes return GFP_ERR_ARG. */
 int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]);
+
+/* Radix schedules of the shared-memory Stockham passes for one precision (GFP_FP64 or GFP_MIXED), one per
+ * axis: nst[r] stages with radices radix[12 r .. 12 r + nst[r] - 1], each in {2, 3, 4, 8, 16}, their
+ * product n_r (unused entries 0).  gfp_set_plans applies schedules read back from gfp_get_plans (e.g. a
+ * tuning cache); a schedule whose product is not n_r, with another radix or more than 12 stages returns
+ * GFP_ERR_ARG.  Lengths with a register-FFT plan use these schedules only in the FP32 transforms of the
+ * mixed solve's FP64 residual. */
+int gfp_get_plans(gfp_grid g, int prec, int radix_out[36], int nst_out[3]);
+int gfp_set_plans(gfp_grid g, int prec, const int radix[36], const int nst[3]);
 
 int gfp_destroy_grid(gfp_grid g);
 

@@ -528,7 +528,6 @@ struct gfp_grid_s {
   double h;
   cudaStream_t stream;
   Dims d;
-  FftPlan plan[3];
   LaunchCfg lc64;
   double* lam = nullptr;
   double* mu = nullptr;
@@ -595,6 +594,8 @@ bool factor_ok(int n) {
   return n == 1;
 }
 
+// Default radix schedule of a length 2^a 3^b: radix-16 stages, then the remaining power of two as one
+// stage (2, 4, 8) or as 8 x 4, then the radix-3 stages.
 FftPlan make_plan(int n) {
   FftPlan p;
   p.n = n;
@@ -602,16 +603,65 @@ FftPlan make_plan(int n) {
   int a = 0, b = 0, m = n;
   while (m % 2 == 0) { m /= 2; ++a; }
   while (m % 3 == 0) { m /= 3; ++b; }
-  int n16 = a / 4, r = a % 4;
-  std::vector<int> rad;
-  if (r == 1 && n16 > 0) { n16 -= 1; rad.push_back(8); rad.push_back(4); }
-  else if (r == 1) rad.push_back(2);
-  else if (r == 2) rad.push_back(4);
-  else if (r == 3) rad.push_back(8);
-  for (int i = 0; i < n16; ++i) rad.insert(rad.begin(), 16);
-  for (int i = 0; i < b; ++i) rad.push_back(3);
-  for (size_t i = 0; i < rad.size(); ++i) p.radix[p.nst++] = rad[i];
+  int n16 = a / 4;
+  const int r = a % 4;
+  int tail[2] = {0, 0}, nt = 0;
+  if (r == 1 && n16 > 0) { n16 -= 1; tail[nt++] = 8; tail[nt++] = 4; }
+  else if (r == 1) tail[nt++] = 2;
+  else if (r == 2) tail[nt++] = 4;
+  else if (r == 3) tail[nt++] = 8;
+  for (int i = 0; i < n16; ++i) p.radix[p.nst++] = 16;
+  for (int i = 0; i < nt; ++i) p.radix[p.nst++] = tail[i];
+  for (int i = 0; i < b; ++i) p.radix[p.nst++] = 3;
   return p;
+}
+
+// A radix schedule is valid when its radices are in {2, 3, 4, 8, 16}, it has at most 12 stages, and
+// their product is n.
+bool plan_ok(const FftPlan& p, int n) {
+  if (p.n != n || p.nst < 0 || p.nst > 12) return false;
+  long long prod = 1;
+  for (int s = 0; s < p.nst; ++s) {
+    const int r = p.radix[s];
+    if (r != 2 && r != 3 && r != 4 && r != 8 && r != 16) return false;
+    prod *= r;
+  }
+  return prod == n;
+}
+
+// Candidate radix schedules of the shared-memory Stockham passes for the autotuner: the power of two
+// split into radices 16, 8 or 4 (the remainder as one smaller stage), the radix-3 stages first or last,
+// and the default; duplicates removed.
+std::vector<FftPlan> plan_candidates(int n) {
+  std::vector<FftPlan> out;
+  auto add = [&](const FftPlan& p) {
+    if (!plan_ok(p, n)) return;
+    for (const FftPlan& q : out)
+      if (q.nst == p.nst && std::equal(q.radix, q.radix + q.nst, p.radix)) return;
+    out.push_back(p);
+  };
+  add(make_plan(n));
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  const int bases[3] = {16, 8, 4};
+  const int logs[3] = {4, 3, 2};
+  for (int k = 0; k < 3; ++k)
+    for (int threes_first = 0; threes_first < 2; ++threes_first) {
+      FftPlan p;
+      p.n = n;
+      p.nst = 0;
+      const int full = a / logs[k], rem = a % logs[k];
+      if (full + (rem ? 1 : 0) + b > 12) continue;
+      if (threes_first)
+        for (int i = 0; i < b; ++i) p.radix[p.nst++] = 3;
+      for (int i = 0; i < full; ++i) p.radix[p.nst++] = bases[k];
+      if (rem) p.radix[p.nst++] = 1 << rem;
+      if (!threes_first)
+        for (int i = 0; i < b; ++i) p.radix[p.nst++] = 3;
+      add(p);
+    }
+  return out;
 }
 
 int round32(int x) { return ((x + 31) / 32) * 32; }
@@ -640,6 +690,9 @@ LaunchCfg make_cfg(const Dims& d, int eb) {
   c.ztmap = nullptr;
   c.z_tma = 0;
   c.x_async = 0;
+  c.plan[0] = make_plan(d.n1);
+  c.plan[1] = make_plan(d.n2);
+  c.plan[2] = make_plan(d.n3);
   return c;
 }
 
@@ -815,17 +868,17 @@ void one_iteration64(gfp_grid g, const GammaParams<double>& gp, int have_delta, 
   const LaunchCfg& lc = lc_override ? *lc_override : g->lc64;
   g->launches += 5;
   const PolarParams pp = fp64_xparams(g);
-  Passes<double>::pass_x(g->stream, lc, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+  Passes<double>::pass_x(g->stream, lc, g->spec, g->eps, g->lam, g->mu, g->tw64[0], lc.plan[0], d,
                          have_delta ? PX_DELTA : 0, nullptr, nullptr, g->st, &pp);
-  Passes<double>::pass_y(g->stream, lc, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
-  Passes<double>::pass_z(g->stream, lc, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+  Passes<double>::pass_y(g->stream, lc, false, g->spec, g->tw64[1], lc.plan[1], d, g->st);
+  Passes<double>::pass_z(g->stream, lc, g->spec, g->tw64[2], lc.plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
                          nullptr);
   if (gp.vprev)
     reduce_crit_kernel<<<1, 1024, 0, g->stream>>>(g->partials, gp.cpart, lc.z_blocks, 1.0 / std::sqrt((double)d.N),
                                                   g->st, g->hist, g->hist_cap);
   else
     launch_reduce_eta(g->stream, g->partials, lc.z_blocks, g->st, g->hist, g->hist_cap);
-  Passes<double>::pass_y(g->stream, lc, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+  Passes<double>::pass_y(g->stream, lc, true, g->spec, g->tw64[1], lc.plan[1], d, g->st);
 }
 
 // resume: continue from the strain set by gfp_set_state; its iteration count K is taken as the
@@ -1032,17 +1085,16 @@ void outer_pass64(cudaStream_t s, const Dims& d, double h, int op, double* eps, 
 // The inner iterations' source v = T_check kt from the residual field r: FP32 transforms along x1
 // (rx_kernel), x2 (the y-pass on three components) and x3 with the stencil phase (rz_kernel).
 void outer_source32(cudaStream_t s, const LaunchCfg& lc32, const Dims& d, int op, const float* rbuf, float2* vsrc,
-                    float2* const* tw32, const FftPlan* plan, float2* const* ph, const SolveState* st,
-                    long long& launches) {
+                    float2* const* tw32, float2* const* ph, const SolveState* st, long long& launches) {
   const long long nlines = (long long)d.n2 * d.n3;
   const int L = 4;
   const size_t smx = sizeof(float2) * 2 * (3 * L / 2) * (size_t)d.n1;
-  rx_kernel<<<(unsigned)((nlines + L - 1) / L), 256, smx, s>>>(rbuf, vsrc, tw32[0], plan[0], d, L, st);
-  Passes<float>::pass_y(s, lc32, false, vsrc, tw32[1], plan[1], d, st, 3);
+  rx_kernel<<<(unsigned)((nlines + L - 1) / L), 256, smx, s>>>(rbuf, vsrc, tw32[0], lc32.plan[0], d, L, st);
+  Passes<float>::pass_y(s, lc32, false, vsrc, tw32[1], lc32.plan[1], d, st, 3);
   const int zc = rz_cols(d.n3);
   const size_t smz = sizeof(float2) * 2 * (size_t)zc * (d.n3 + 1);
   const bool phase = res_stencil(op) == RS_AFD;
-  rz_kernel<<<dim3((d.n1h + zc - 1) / zc, d.n2, 3), 256, smz, s>>>(vsrc, tw32[2], plan[2], d, zc,
+  rz_kernel<<<dim3((d.n1h + zc - 1) / zc, d.n2, 3), 256, smz, s>>>(vsrc, tw32[2], lc32.plan[2], d, zc,
                                                                    phase ? ph[0] : nullptr, phase ? ph[1] : nullptr,
                                                                    phase ? ph[2] : nullptr, st);
   launches += 3;
@@ -1055,7 +1107,7 @@ void residual_pass64(gfp_grid g, int op, bool with_corr) {
 }
 
 void inner_source32(gfp_grid g, int op) {
-  outer_source32(g->stream, g->lc32, g->d, op, reinterpret_cast<const float*>(g->spec), g->vsrc, g->tw32, g->plan,
+  outer_source32(g->stream, g->lc32, g->d, op, reinterpret_cast<const float*>(g->spec), g->vsrc, g->tw32,
                  g->ph32, g->st, g->launches);
 }
 
@@ -1065,13 +1117,13 @@ void inner_iteration32(gfp_grid g, const GammaParams<float>& gp, int flags) {
   const Dims& d = g->d;
   g->launches += 5;
   float2* spec32 = reinterpret_cast<float2*>(g->spec);
-  Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, flags,
+  Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->lc32.plan[0], d, flags,
                         nullptr, nullptr, g->st_in);
-  Passes<float>::pass_y(g->stream, g->lc32, false, spec32, g->tw32[1], g->plan[1], d, g->st_in);
-  Passes<float>::pass_z(g->stream, g->lc32, spec32, g->tw32[2], g->plan[2], d, gp, g->partials, g->st_in, PZ_INNER,
+  Passes<float>::pass_y(g->stream, g->lc32, false, spec32, g->tw32[1], g->lc32.plan[1], d, g->st_in);
+  Passes<float>::pass_z(g->stream, g->lc32, spec32, g->tw32[2], g->lc32.plan[2], d, gp, g->partials, g->st_in, PZ_INNER,
                         g->vsrc);
   launch_reduce_eta(g->stream, g->partials, g->lc32.z_blocks, g->st_in, nullptr, 0);
-  Passes<float>::pass_y(g->stream, g->lc32, true, spec32, g->tw32[1], g->plan[1], d, g->st_in);
+  Passes<float>::pass_y(g->stream, g->lc32, true, spec32, g->tw32[1], g->lc32.plan[1], d, g->st_in);
 }
 
 const double kInnerReduction = 1e-4;  // target of one inner solve relative to the FP64 residual
@@ -1302,15 +1354,15 @@ int solve_dgo(gfp_grid g, const gfp_scheme* sc, const double E[6], double tol, i
     const int nb = std::min(chunk, maxit + 1 - launched);
     for (int b = 0; b < nb; ++b) {
       const int j = launched + b;
-      Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+      Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->lc64.plan[0], d,
                              (stress_form ? PX_DRES : PX_POLAR) | (j > 0 ? PX_DELTA : 0), nullptr, nullptr, g->st,
                              &pp);
       if (j > 0) reduce_dgo_kernel<<<1, 256, 0, g->stream>>>(g->xpart, np, enorm, g->st, g->hist, g->hist_cap);
       g->launches += j > 0 ? 5 : 4;
-      Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
-      Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_DGO,
+      Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->lc64.plan[1], d, g->st);
+      Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->lc64.plan[2], d, gp, g->partials, g->st, PZ_DGO,
                              nullptr);
-      Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+      Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->lc64.plan[1], d, g->st);
     }
     launched += nb;
     GFP_CU(cudaGetLastError());
@@ -1387,27 +1439,6 @@ int noalloc_scratch(void** out) {
   return GFP_OK;
 }
 
-// Same stage radices as make_plan, without heap storage.
-FftPlan make_plan_fixed(int n) {
-  FftPlan p;
-  p.n = n;
-  p.nst = 0;
-  int a = 0, b = 0, m = n;
-  while (m % 2 == 0) { m /= 2; ++a; }
-  while (m % 3 == 0) { m /= 3; ++b; }
-  int n16 = a / 4;
-  const int r = a % 4;
-  int tail[2] = {0, 0}, nt = 0;
-  if (r == 1 && n16 > 0) { n16 -= 1; tail[nt++] = 8; tail[nt++] = 4; }
-  else if (r == 1) tail[nt++] = 2;
-  else if (r == 2) tail[nt++] = 4;
-  else if (r == 3) tail[nt++] = 8;
-  for (int i = 0; i < n16; ++i) p.radix[p.nst++] = 16;
-  for (int i = 0; i < nt; ++i) p.radix[p.nst++] = tail[i];
-  for (int i = 0; i < b; ++i) p.radix[p.nst++] = 3;
-  return p;
-}
-
 // One entry of the per-axis tables (same values as build_tables).
 void table_entry(int op, int n, int i, double h, double* A, double* B) {
   const double pi = 3.14159265358979323846;
@@ -1480,7 +1511,6 @@ int gfp_create_grid(int n1, int n2, int n3, double h, void* cuda_stream, gfp_gri
   d.N = (long long)n1 * n2 * n3;
   d.S = (long long)n3 * n2 * d.P;
   const int ns[3] = {n1, n2, n3};
-  for (int r = 0; r < 3; ++r) g->plan[r] = make_plan(ns[r]);
   g->lc64 = make_cfg(d, 16);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
@@ -1624,13 +1654,13 @@ int gfp_get_displacement(gfp_grid g, const gfp_scheme* sc, double* dst, int wher
   *g->st_host = s0;
   GFP_CU(cudaMemcpyAsync(g->st, g->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, g->stream));
   // forward transform of eps - E_bar, u^ per mode, inverse transform of its 3 components
-  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_STRAIN,
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->lc64.plan[0], d, PX_STRAIN,
                          nullptr, nullptr, g->st, &pp);
-  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
-  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_DISP,
+  Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->lc64.plan[1], d, g->st);
+  Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->lc64.plan[2], d, gp, g->partials, g->st, PZ_DISP,
                          nullptr);
-  Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
-  Passes<double>::pass_x(g->stream, g->lc64, g->spec, out, g->lam, g->mu, g->tw64[0], g->plan[0], d,
+  Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->lc64.plan[1], d, g->st);
+  Passes<double>::pass_x(g->stream, g->lc64, g->spec, out, g->lam, g->mu, g->tw64[0], g->lc64.plan[0], d,
                          PX_DELTA | PX_OUTPUT, nullptr, nullptr, g->st, &pp);
   GFP_CU(cudaGetLastError());
   if (where == 0) GFP_CU(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, g->stream));
@@ -1764,27 +1794,27 @@ int gfp_time_passes(gfp_grid g, const gfp_scheme* sc, int iters, double pass_ms[
   for (int it = 0; it < iters; ++it) {
     GFP_CU(cudaEventRecord(ev[0], g->stream));
     if (mixed)
-      Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d,
+      Passes<float>::pass_x(g->stream, g->lc32, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->lc32.plan[0], d,
                             PX_DELTA, nullptr, nullptr, g->st_in);
     else
-      Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_DELTA,
+      Passes<double>::pass_x(g->stream, g->lc64, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->lc64.plan[0], d, PX_DELTA,
                              nullptr, nullptr, g->st);
     GFP_CU(cudaEventRecord(ev[1], g->stream));
-    if (mixed) Passes<float>::pass_y(g->stream, g->lc32, false, spec32, g->tw32[1], g->plan[1], d, g->st_in);
-    else Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    if (mixed) Passes<float>::pass_y(g->stream, g->lc32, false, spec32, g->tw32[1], g->lc32.plan[1], d, g->st_in);
+    else Passes<double>::pass_y(g->stream, g->lc64, false, g->spec, g->tw64[1], g->lc64.plan[1], d, g->st);
     GFP_CU(cudaEventRecord(ev[2], g->stream));
     if (mixed)
-      Passes<float>::pass_z(g->stream, g->lc32, spec32, g->tw32[2], g->plan[2], d, gp32, g->partials, g->st_in,
+      Passes<float>::pass_z(g->stream, g->lc32, spec32, g->tw32[2], g->lc32.plan[2], d, gp32, g->partials, g->st_in,
                             PZ_INNER, g->vsrc);
     else
-      Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+      Passes<double>::pass_z(g->stream, g->lc64, g->spec, g->tw64[2], g->lc64.plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
                              nullptr);
     GFP_CU(cudaEventRecord(ev[3], g->stream));
     if (mixed) launch_reduce_eta(g->stream, g->partials, g->lc32.z_blocks, g->st_in, nullptr, 0);
     else launch_reduce_eta(g->stream, g->partials, g->lc64.z_blocks, g->st, nullptr, 0);
     GFP_CU(cudaEventRecord(ev[4], g->stream));
-    if (mixed) Passes<float>::pass_y(g->stream, g->lc32, true, spec32, g->tw32[1], g->plan[1], d, g->st_in);
-    else Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->plan[1], d, g->st);
+    if (mixed) Passes<float>::pass_y(g->stream, g->lc32, true, spec32, g->tw32[1], g->lc32.plan[1], d, g->st_in);
+    else Passes<double>::pass_y(g->stream, g->lc64, true, g->spec, g->tw64[1], g->lc64.plan[1], d, g->st);
     GFP_CU(cudaEventRecord(ev[5], g->stream));
     GFP_CU(cudaEventSynchronize(ev[5]));
     for (int k = 0; k < 5; ++k) {
@@ -1937,8 +1967,6 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
   gp.nyq_avg = (sc->op == OP_F || sc->op == OP_HC) ? 1 : 0;
   gp.half_shift = 0;
   gp.dgo = nullptr;
-  FftPlan plan[3];
-  for (int r = 0; r < 3; ++r) plan[r] = make_plan_fixed(ns[r]);
   // the shared scratch keeps the previous call's contents: clear the spectrum, reset the state
   GFP_CU(cudaMemsetAsync(spec, 0, sizeof(double2) * 6 * (size_t)d.S, stream));
   fill_eps_kernel<<<(int)std::min<long long>(4096, (d.N + 255) / 256), 256, 0, stream>>>(eps, d.N, E[0], E[1], E[2],
@@ -1956,11 +1984,11 @@ int gfp_solve_noalloc(int n1, int n2, int n3, double h, const double* lambda, co
     const int nb = std::min(chunk, maxit - launched);
     for (int b = 0; b < nb; ++b) {
       const int flags = (launched + b) > 0 ? PX_DELTA : 0;
-      Passes<double>::pass_x(stream, lc, spec, eps, lambda, mu, tw[0], plan[0], d, flags, nullptr, nullptr, st);
-      Passes<double>::pass_y(stream, lc, false, spec, tw[1], plan[1], d, st);
-      Passes<double>::pass_z(stream, lc, spec, tw[2], plan[2], d, gp, partials, st, PZ_GAMMA, nullptr);
+      Passes<double>::pass_x(stream, lc, spec, eps, lambda, mu, tw[0], lc.plan[0], d, flags, nullptr, nullptr, st);
+      Passes<double>::pass_y(stream, lc, false, spec, tw[1], lc.plan[1], d, st);
+      Passes<double>::pass_z(stream, lc, spec, tw[2], lc.plan[2], d, gp, partials, st, PZ_GAMMA, nullptr);
       launch_reduce_eta(stream, partials, lc.z_blocks, st, nullptr, 0);
-      Passes<double>::pass_y(stream, lc, true, spec, tw[1], plan[1], d, st);
+      Passes<double>::pass_y(stream, lc, true, spec, tw[1], lc.plan[1], d, st);
     }
     launched += nb;
     GFP_CU(cudaGetLastError());
@@ -2009,20 +2037,20 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     for (int i = 0; i < iters; ++i) {
       if (pass == 0) {
         if (mixed)
-          Passes<float>::pass_x(g->stream, c, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, PX_DELTA,
+          Passes<float>::pass_x(g->stream, c, spec32, g->eps32, g->lam32, g->mu32, g->tw32[0], c.plan[0], d, PX_DELTA,
                                 nullptr, nullptr, g->st_in);
         else
-          Passes<double>::pass_x(g->stream, c, g->spec, g->eps, g->lam, g->mu, g->tw64[0], g->plan[0], d, PX_DELTA,
+          Passes<double>::pass_x(g->stream, c, g->spec, g->eps, g->lam, g->mu, g->tw64[0], c.plan[0], d, PX_DELTA,
                                  nullptr, nullptr, g->st);
       } else if (pass == 1) {
-        if (mixed) Passes<float>::pass_y(g->stream, c, false, spec32, g->tw32[1], g->plan[1], d, g->st_in);
-        else Passes<double>::pass_y(g->stream, c, false, g->spec, g->tw64[1], g->plan[1], d, g->st);
+        if (mixed) Passes<float>::pass_y(g->stream, c, false, spec32, g->tw32[1], c.plan[1], d, g->st_in);
+        else Passes<double>::pass_y(g->stream, c, false, g->spec, g->tw64[1], c.plan[1], d, g->st);
       } else {
         if (mixed)
-          Passes<float>::pass_z(g->stream, c, spec32, g->tw32[2], g->plan[2], d, gp32, g->partials, g->st_in,
+          Passes<float>::pass_z(g->stream, c, spec32, g->tw32[2], c.plan[2], d, gp32, g->partials, g->st_in,
                                 PZ_INNER, g->vsrc);
         else
-          Passes<double>::pass_z(g->stream, c, g->spec, g->tw64[2], g->plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
+          Passes<double>::pass_z(g->stream, c, g->spec, g->tw64[2], c.plan[2], d, gp, g->partials, g->st, PZ_GAMMA,
                                  nullptr);
       }
     }
@@ -2086,6 +2114,24 @@ int gfp_tune(gfp_grid g, const gfp_scheme* sc, int iters, int tiles_out[3]) {
     lc = best;
     refresh_ztmap(g, mixed);
   }
+  // radix schedules of the shared-memory Stockham passes, on the axes without a register-FFT plan
+  {
+    const int ns[3] = {d.n1, d.n2, d.n3};
+    for (int r = 0; r < 3; ++r) {
+      if (has_register_plan(ns[r])) continue;
+      const std::vector<FftPlan> cands = plan_candidates(ns[r]);
+      if (cands.size() < 2) continue;
+      LaunchCfg best = lc;
+      float bt = run(r, lc);
+      for (const FftPlan& p : cands) {
+        LaunchCfg c = lc;
+        c.plan[r] = p;
+        const float t = run(r, c);
+        if (t < bt) { bt = t; best = c; }
+      }
+      lc = best;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (tiles_out) {
@@ -2124,6 +2170,38 @@ int gfp_set_tiles(gfp_grid g, int prec, const int tiles[3]) {
   lc.z_tma = tiles[2] < 0 ? 1 : 0;
   finalize_cfg(d, lc);
   refresh_ztmap(g, mixed);
+  ++g->phase_gen;
+  return GFP_OK;
+}
+
+// Radix schedules of the shared-memory Stockham passes (one per axis) for one precision.
+int gfp_get_plans(gfp_grid g, int prec, int radix_out[36], int nst_out[3]) {
+  if (!g || !radix_out || !nst_out || (prec != GFP_FP64 && prec != GFP_MIXED)) return GFP_ERR_ARG;
+  const LaunchCfg& lc = prec == GFP_MIXED ? g->lc32 : g->lc64;
+  for (int r = 0; r < 3; ++r) {
+    nst_out[r] = lc.plan[r].nst;
+    for (int s = 0; s < 12; ++s) radix_out[12 * r + s] = s < lc.plan[r].nst ? lc.plan[r].radix[s] : 0;
+  }
+  return GFP_OK;
+}
+
+int gfp_set_plans(gfp_grid g, int prec, const int radix[36], const int nst[3]) {
+  if (!g || !radix || !nst || (prec != GFP_FP64 && prec != GFP_MIXED)) return GFP_ERR_ARG;
+  if (prec == GFP_MIXED) {
+    int rc = ensure_mixed(g);
+    if (rc) return rc;
+  }
+  const int ns[3] = {g->n1, g->n2, g->n3};
+  FftPlan p[3];
+  for (int r = 0; r < 3; ++r) {
+    if (nst[r] < 0 || nst[r] > 12) return GFP_ERR_ARG;
+    p[r].n = ns[r];
+    p[r].nst = nst[r];
+    for (int s = 0; s < 12; ++s) p[r].radix[s] = s < nst[r] ? radix[12 * r + s] : 0;
+    if (!plan_ok(p[r], ns[r])) return GFP_ERR_ARG;
+  }
+  LaunchCfg& lc = prec == GFP_MIXED ? g->lc32 : g->lc64;
+  for (int r = 0; r < 3; ++r) lc.plan[r] = p[r];
   ++g->phase_gen;
   return GFP_OK;
 }
@@ -2177,17 +2255,17 @@ void slot_window(BatchSlot& s, int op, const GammaParams<float>& gp32, const Bat
   long long launches = 0;
   outer_pass64(st, d, g->h, op, s.eps, g->lam, g->mu, nullptr, s.eps32, s.cmean, reinterpret_cast<float*>(s.spec),
                s.rpart, s.partials, s.st, launches);
-  outer_source32(st, s.lc32, d, op, reinterpret_cast<const float*>(s.spec), s.vsrc, g->tw32, g->plan, g->ph32, s.st,
+  outer_source32(st, s.lc32, d, op, reinterpret_cast<const float*>(s.spec), s.vsrc, g->tw32, g->ph32, s.st,
                  launches);
   batch_arm_kernel<<<1, 32, 0, st>>>(s.st, s.st_in, s.acc, ctl, kInnerReduction, window);
   float2* spec32 = reinterpret_cast<float2*>(s.spec);
   for (int k = 0; k < window; ++k) {
-    Passes<float>::pass_x(st, s.lc32, spec32, s.eps32, g->lam32, g->mu32, g->tw32[0], g->plan[0], d, PX_DELTA,
+    Passes<float>::pass_x(st, s.lc32, spec32, s.eps32, g->lam32, g->mu32, g->tw32[0], s.lc32.plan[0], d, PX_DELTA,
                           nullptr, nullptr, s.st_in);
-    Passes<float>::pass_y(st, s.lc32, false, spec32, g->tw32[1], g->plan[1], d, s.st_in);
-    Passes<float>::pass_z(st, s.lc32, spec32, g->tw32[2], g->plan[2], d, gp32, s.partials, s.st_in, PZ_INNER, s.vsrc);
+    Passes<float>::pass_y(st, s.lc32, false, spec32, g->tw32[1], s.lc32.plan[1], d, s.st_in);
+    Passes<float>::pass_z(st, s.lc32, spec32, g->tw32[2], s.lc32.plan[2], d, gp32, s.partials, s.st_in, PZ_INNER, s.vsrc);
     launch_reduce_eta(st, s.partials, s.lc32.z_blocks, s.st_in, nullptr, 0);
-    Passes<float>::pass_y(st, s.lc32, true, spec32, g->tw32[1], g->plan[1], d, s.st_in);
+    Passes<float>::pass_y(st, s.lc32, true, spec32, g->tw32[1], s.lc32.plan[1], d, s.st_in);
   }
   corr_mean_partial_kernel<<<cvb, 256, 0, st>>>(s.eps32, d.N, s.cpart, s.st_in);
   corr_mean_final_kernel<<<1, 32, 0, st>>>(s.cpart, cvb, d.N, s.cmean, s.st_in);

@@ -619,6 +619,16 @@ __global__ void pass_z_gamma_kernel(typename C<R>::T* __restrict__ spec, const t
 // --------------------------------------------------------------------------------------------
 // Launch configuration and host-side launchers (instantiated per precision in gfp_k64.cu / gfp_k32.cu)
 // --------------------------------------------------------------------------------------------
+// Lengths with a compile-time register-FFT plan (CPlan in gfp_fftc.cuh); other lengths 2^a 3^b run the
+// shared-memory Stockham kernels with a runtime radix schedule.
+#define GFP_FOR_CSIZES(X) X(32) X(64) X(96) X(128) X(192) X(256) X(512)
+inline bool has_register_plan(int n) {
+#define GFP_CS(N_) if (n == N_) return true;
+  GFP_FOR_CSIZES(GFP_CS)
+#undef GFP_CS
+  return false;
+}
+
 struct LaunchCfg {
   int x_lines, x_threads;   // generic x-pass
   int y_cols, y_threads;
@@ -628,6 +638,8 @@ struct LaunchCfg {
   const void* ztmap;        // host CUtensorMap of the spectrum for TMA z-tiles of z_cols columns, or null
   int z_tma;                // use the TMA-fed z-pass when eligible (1) or the register-FFT one (0)
   int x_async;              // register-FFT x-pass with cp.async staging (1) or direct loads (0)
+  FftPlan plan[3];          // radix schedules of the shared-memory Stockham passes per axis (lengths
+                            // without a register-FFT plan), chosen by the autotuner
 };
 
 template <typename R>

@@ -6,8 +6,6 @@
 
 namespace gfp {
 
-#define GFP_FOR_CSIZES(X) X(32) X(64) X(96) X(128) X(192) X(256) X(512)
-
 template <typename R>
 cudaError_t Passes<R>::setup() {
   const int mx = 220 * 1024;  // below the 227 KB opt-in limit, leaving room for static shared memory

@@ -48,7 +48,8 @@ EXPORTS = ("gfp_create_grid", "gfp_set_phases", "gfp_solve", "gfp_get_strain", "
            "gfp_grad", "gfp_get_state", "gfp_set_state", "gfp_destroy_grid", "gfp_error_string",
            "gfp_time_passes", "gfp_last_error_detail", "gfp_solve_noalloc", "gfp_tune", "gfp_set_tiles",
            "gfp_solve_batch", "gfp_set_fault_injection", "gfp_set_eigenstrain", "gfp_get_displacement",
-           "gfp_measure_fma_peak", "gfp_batch_create", "gfp_batch_solve", "gfp_batch_destroy")
+           "gfp_measure_fma_peak", "gfp_batch_create", "gfp_batch_solve", "gfp_batch_destroy", "gfp_get_plans",
+           "gfp_set_plans")
 
 
 def lib():
@@ -83,6 +84,8 @@ def lib():
     L.gfp_set_fault_injection.argtypes = [ip, ip]
     L.gfp_measure_fma_peak.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
     L.gfp_set_tiles.argtypes = [vp, ip, vp]
+    L.gfp_get_plans.argtypes = [vp, ip, vp, vp]
+    L.gfp_set_plans.argtypes = [vp, ip, vp, vp]
     L.gfp_set_eigenstrain.argtypes = [vp, vp, ip]
     L.gfp_get_displacement.argtypes = [vp, ctypes.POINTER(Scheme), vp, ip]
     L.gfp_last_error_detail.argtypes = []
@@ -260,10 +263,11 @@ class Grid:
         return ms
 
     def tune(self, sch, iters=5, cache=None):
-        """Choose tile shapes with the native autotuner, or reuse them from a JSON cache.
+        """Choose tile shapes and radix schedules with the native autotuner, or reuse them from a JSON cache.
 
         cache: path of a JSON file (default: $GFP_TUNE_CACHE if set); entries are keyed by grid size,
-        precision and GPU name.
+        precision and GPU name (the tiles) and by the same key + ":plans" (the radix schedules).
+        Returns the tiles.
         """
         import json
         prec = sch.prec
@@ -279,14 +283,35 @@ class Grid:
         if key in table:
             tiles = (ctypes.c_int * 3)(*table[key])
             _check(lib().gfp_set_tiles(self._h, int(prec), ctypes.cast(tiles, ctypes.c_void_p)), "gfp_set_tiles")
+            if key + ":plans" in table:
+                self.set_plans(prec, table[key + ":plans"])
             return list(table[key])
         out = (ctypes.c_int * 3)()
         _check(lib().gfp_tune(self._h, ctypes.byref(sch), int(iters), ctypes.cast(out, ctypes.c_void_p)), "gfp_tune")
         if path:
             table[key] = list(out)
+            table[key + ":plans"] = self.get_plans(prec)
             with open(path, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)
         return list(out)
+
+    def get_plans(self, prec):
+        """Radix schedules [axis][stage] of the shared-memory Stockham passes for one precision."""
+        rad = (ctypes.c_int * 36)()
+        nst = (ctypes.c_int * 3)()
+        _check(lib().gfp_get_plans(self._h, int(prec), ctypes.cast(rad, ctypes.c_void_p),
+                                   ctypes.cast(nst, ctypes.c_void_p)), "gfp_get_plans")
+        return [[rad[12 * r + s] for s in range(nst[r])] for r in range(3)]
+
+    def set_plans(self, prec, plans):
+        rad = (ctypes.c_int * 36)()
+        nst = (ctypes.c_int * 3)()
+        for r, p in enumerate(plans):
+            nst[r] = len(p)
+            for s, v in enumerate(p[:12]):
+                rad[12 * r + s] = int(v)
+        _check(lib().gfp_set_plans(self._h, int(prec), ctypes.cast(rad, ctypes.c_void_p),
+                                   ctypes.cast(nst, ctypes.c_void_p)), "gfp_set_plans")
 
     def set_tiles(self, prec, tiles):
         t = (ctypes.c_int * 3)(*[int(v) for v in tiles])
