@@ -687,16 +687,22 @@ __global__ void __launch_bounds__(512) pass_x_c_kernel(typename C<R>::T* __restr
 }
 
 // ------------------------------------------------------------------------------------------------
-// pass_x with asynchronous staging of the real rows: at its start the CTA issues cp.async copies (16-byte
-// granules, L2 only) of its strain rows and Lame rows into shared memory, loads the spectrum rows into
-// registers and runs the inverse transform while those copies are in flight; the update then reads the
-// staged rows.  The same transform / update / stress / transform sequence as pass_x_c_kernel.
+// pass_x with asynchronous staging: the CTA first copies its spectrum rows, strain rows and Lame
+// rows into shared memory with cp.async (16-byte granules, L2 only), so that all loads are in flight
+// at once, then runs the same transform / update / stress / transform sequence as pass_x_c_kernel
+// from shared memory.  Meant for small CTAs (few lines), several resident per SM.
 // ------------------------------------------------------------------------------------------------
+
+template <typename R, int N>
+__host__ __device__ constexpr int xa_spec_pitch() {  // complex elements per staged spectrum row (16-byte multiple)
+  return ((N / 2 + 1) * (int)sizeof(typename C<R>::T) + 15) / 16 * 16 / (int)sizeof(typename C<R>::T);
+}
 
 template <typename R, int N>
 __host__ __device__ constexpr size_t xa_smem_bytes(int lines) {
   typedef typename C<R>::T T;
-  return sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16)) + sizeof(R) * (size_t)(8 * lines * N);
+  return sizeof(T) * (size_t)(N + 3 * lines * (N + N / 16) + 6 * lines * xa_spec_pitch<R, N>()) +
+         sizeof(R) * (size_t)(8 * lines * N);
 }
 
 template <typename R, int N>
@@ -712,54 +718,65 @@ __global__ void __launch_bounds__(512) pass_x_a_kernel(typename C<R>::T* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int LP = N + N / 16;
   constexpr int NH = N / 2 + 1;
-  T* twl = reinterpret_cast<T*>(smem_raw);                   // [N]
+  constexpr int SP = xa_spec_pitch<R, N>();
+  T* sspec = reinterpret_cast<T*>(smem_raw);                 // [6][lines][SP]
+  T* twl = sspec + 6 * lines * SP;                           // [N]
   T* buf = twl + N;                                          // [3 lines][LP]
   R* sst = reinterpret_cast<R*>(buf + 3 * lines * LP);       // [8][lines][N]: eps 0..5, lambda, mu
   const long long nlines = (long long)d.n2 * d.n3;
   const long long line0 = (long long)blockIdx.x * lines;
   const bool zero = (flags & PX_ZERO) != 0 || st->restart;
   const bool have_delta = (flags & PX_DELTA) != 0 && !st->restart;
-  // ---- the real rows this CTA reads, in flight during the inverse transform
+  // ---- stage everything this CTA reads
   {
-    constexpr int row_chunks = N * (int)sizeof(R) / 16;      // 16-byte granules per real row
+    constexpr int spec_chunks = SP * (int)sizeof(T) / 16;     // 16-byte granules per spectrum row
+    constexpr int row_chunks = N * (int)sizeof(R) / 16;      // per real row
+    const int nsp = have_delta ? 6 * lines * spec_chunks : 0;
     const int nre = (zero ? 2 : 8) * lines * row_chunks;
-    for (int j = threadIdx.x; j < nre; j += blockDim.x) {
-      const int ch = j % row_chunks, ql = j / row_chunks;
-      const int l = ql % lines, q0 = ql / lines;
-      const int q = zero ? 6 + q0 : q0;
-      const long long li = line0 + l;
-      if (li >= nlines) continue;
-      const R* src = q < 6 ? eps + q * d.N + li * N : (q == 6 ? lam + li * N : mu + li * N);
-      cp_async16(reinterpret_cast<unsigned char*>(sst + (q * lines + l) * N) + 16 * ch,
-                 reinterpret_cast<const unsigned char*>(src) + 16 * ch);
+    for (int i = threadIdx.x; i < nsp + nre; i += blockDim.x) {
+      if (i < nsp) {
+        const int ch = i % spec_chunks, cl = i / spec_chunks;
+        const int l = cl % lines, c = cl / lines;
+        const long long li = line0 + l;
+        if (li >= nlines) continue;
+        cp_async16(reinterpret_cast<unsigned char*>(sspec + (c * lines + l) * SP) + 16 * ch,
+                   reinterpret_cast<const unsigned char*>(spec + c * d.S + d.xrow(li) * d.P) + 16 * ch);
+      } else {
+        const int j = i - nsp;
+        const int ch = j % row_chunks, ql = j / row_chunks;
+        const int l = ql % lines, q0 = ql / lines;
+        const int q = zero ? 6 + q0 : q0;
+        const long long li = line0 + l;
+        if (li >= nlines) continue;
+        const R* src = q < 6 ? eps + q * d.N + li * N : (q == 6 ? lam + li * N : mu + li * N);
+        cp_async16(reinterpret_cast<unsigned char*>(sst + (q * lines + l) * N) + 16 * ch,
+                   reinterpret_cast<const unsigned char*>(src) + 16 * ch);
+      }
     }
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) twl[i] = tw[i];
+  cp_async_wait_all();
+  __syncthreads();
   const int t = threadIdx.x % P::T, fl = threadIdx.x / P::T;   // fl = pair * lines + l
   const int p = fl / lines, l = fl % lines;
-  const long long li = line0 + l;
-  const bool live = (fl < 3 * lines) && (li < nlines);
   const SLine<T, true> sl{buf + fl * LP, 1};
   T v[P::E];
   if (have_delta) {
-    const T* A = spec + (2 * p) * d.S + d.xrow(li) * d.P;
-    const T* B = spec + (2 * p + 1) * d.S + d.xrow(li) * d.P;
+    const T* A = sspec + (2 * p * lines + l) * SP;
+    const T* B = sspec + ((2 * p + 1) * lines + l) * SP;
 #pragma unroll
     for (int b = 0; b < P::E / P::R(0); ++b)
 #pragma unroll
       for (int r = 0; r < P::R(0); ++r) {
         const int x = cin_idx<N, 0>(t, b, r);
-        T z; z.x = 0; z.y = 0;
-        if (live) {
-          const int k = x < NH ? x : N - x;
-          T a = A[k], bb = B[k];
-          if (k == 0 || 2 * k == N) { a.y = 0; bb.y = 0; }
-          if (x < NH) { z.x = a.x - bb.y; z.y = a.y + bb.x; }      // A + iB
-          else { z.x = a.x + bb.y; z.y = -a.y + bb.x; }            // conj(A) + i conj(B)
-        }
+        const int k = x < NH ? x : N - x;
+        T a = A[k], bb = B[k];
+        if (k == 0 || 2 * k == N) { a.y = 0; bb.y = 0; }
+        T z;
+        if (x < NH) { z.x = a.x - bb.y; z.y = a.y + bb.x; }      // A + iB
+        else { z.x = a.x + bb.y; z.y = -a.y + bb.x; }            // conj(A) + i conj(B)
         v[b * P::R(0) + r] = z;
       }
-    __syncthreads();
     cfft<N, true>(v, sl, t, twl);
     constexpr int RL = P::R(P::NST - 1);
 #pragma unroll
@@ -767,7 +784,6 @@ __global__ void __launch_bounds__(512) pass_x_a_kernel(typename C<R>::T* __restr
 #pragma unroll
       for (int r = 0; r < RL; ++r) sl[cout_idx<N, P::NST - 1>(t, b, r)] = v[b * RL + r];
   }
-  cp_async_wait_all();
   __syncthreads();
   double cm[6];
   if (corr) {
