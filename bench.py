@@ -47,8 +47,8 @@ def ncu_traffic(kernel, n, prec, tiles):
         return None
     sha = kernel_sources_sha1()
     for rec in recs:
-        if (rec["kernel"], rec["n"], rec["prec"], list(rec["tiles"])) == (kernel, n, prec, list(tiles or [])) \
-                and rec["sources_sha1"] == sha:
+        key = (rec.get("kernel"), rec.get("n"), rec.get("prec"), list(rec.get("tiles") or []))
+        if key == (kernel, n, prec, list(tiles or [])) and rec.get("sources_sha1") == sha:
             return rec["dram_read_bytes"] + rec["dram_write_bytes"]
     return None
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
