@@ -282,14 +282,21 @@ __device__ __forceinline__ void rot_right(V* a, int s) {
 // position (t + j) mod T (already multiplied by its twiddle w_N^{s t} at the sender), which a register
 // rotation by t puts in order.  Tables in shared memory, read by consecutive lanes at compile-time
 // offsets: rt[m T + t] = w_T^{m t} and tw3[j T + t] = w_N^{t ((t - j) mod T)} (forward sign).
-template <int N, bool INV>
+// Phased forms: without ROT the final rotation is skipped, and since lane t's stage-1 inputs then sit
+// at positions (t + j) mod T, output k comes out as w^{-t k} X[t + T k] = conj(rt[t + T k]) X (forward
+// sign); without PRE the input scaling by w^{m t} is skipped, i.e. the inputs must arrive already
+// multiplied by it -- which is exactly what a phased forward output, passed through a pointwise linear
+// step with real coefficients, is for the inverse transform (w_inv^{m t} = conj(w_fwd^{m t})).
+template <int N, bool INV, bool PRE = true, bool ROT = true>
 __device__ __forceinline__ void sfft(float2* v, int t, int h, const float2* tw3, const float2* rt) {
   constexpr int T_ = CPlan<N>::T, LPW = 32 / T_;
+  if (PRE) {
 #pragma unroll
-  for (int m = 1; m < T_; ++m) {  // x_m w^{m t}
-    float2 w = rt[m * T_ + t];
-    if (INV) w.y = -w.y;
-    v[m] = cmul(v[m], w);
+    for (int m = 1; m < T_; ++m) {  // x_m w^{m t}
+      float2 w = rt[m * T_ + t];
+      if (INV) w.y = -w.y;
+      v[m] = cmul(v[m], w);
+    }
   }
   Dft<T_, !INV, float2>::run(v);  // v[j] = y_{(t - j) mod T}, destined to lane (t - j) mod T
 #pragma unroll
@@ -306,7 +313,7 @@ __device__ __forceinline__ void sfft(float2* v, int t, int h, const float2* tw3,
     w.y = __shfl_sync(0xffffffffu, v[j].y, src);
     v[j] = w;
   }
-  rot_right<T_>(v, t);  // v[s] = stage-1 input s
+  if (ROT) rot_right<T_>(v, t);  // v[s] = stage-1 input s
   Dft<T_, INV, float2>::run(v);
 }
 
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
     float2 v[T_];
 #pragma unroll
     for (int r = 0; r < T_; ++r) v[r] = el(c, t + T_ * r, col);
-    sfft<N, false>(v, t, h, twl, roots);
+    sfft<N, false, true, false>(v, t, h, twl, roots);  // phased output: conj(roots[z]) X[z]
 #pragma unroll
     for (int k = 0; k < T_; ++k) el(c, t + T_ * k, col) = v[k];
   }
@@ -435,8 +442,13 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
         const float kt1 = a1 * b2 * ab.y, kt2 = a2 * ab.y * b1, kt3 = ab.x * b1 * b2;
         float2 v1, v2, v3;
         tk_vec<float>(tt, kt1, kt2, kt3, v1, v2, v3);
+        // the tile holds conj(roots[z]) X[z] (phased forward transform): the Green step is linear with real
+        // coefficients and |v|^2 ignores a common phase, so only the source needs the same phase
         const float2* s3 = src[q % GB];
-        v1.x += s3[0].x; v1.y += s3[0].y; v2.x += s3[1].x; v2.y += s3[1].y; v3.x += s3[2].x; v3.y += s3[2].y;
+        float2 ph = roots[z];
+        ph.y = -ph.y;
+        const float2 p1 = cmul(s3[0], ph), p2 = cmul(s3[1], ph), p3 = cmul(s3[2], ph);
+        v1.x += p1.x; v1.y += p1.y; v2.x += p2.x; v2.y += p2.y; v3.x += p3.x; v3.y += p3.y;
         float r2 = vnorm2(v1, v2, v3);
         acc += self1 ? r2 : 2.f * r2;
         gamma0_from_v<float>(v1, v2, v3, kt1, kt2, kt3, gp.c_mu, gp.c_lm, gp.invN, o);
@@ -464,7 +476,7 @@ __global__ void __launch_bounds__(24 * CPlan<N>::T, 2) pass_z_s_kernel(const __g
     float2 v[T_];
 #pragma unroll
     for (int r = 0; r < T_; ++r) v[r] = el(c, t + T_ * r, col);
-    sfft<N, true>(v, t, h, twl, roots);
+    sfft<N, true, false, true>(v, t, h, twl, roots);   // phased input, true output
 #pragma unroll
     for (int k = 0; k < T_; ++k) el(c, t + T_ * k, col) = v[k];
   }
