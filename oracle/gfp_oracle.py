@@ -364,6 +364,14 @@ class Result:
         self.converged = converged
 
 
+def _ratio(num, den):
+    """A residual num / den; with a zero reference (zero mean strain and no eigenstrain: the stress vanishes
+    identically) a zero numerator is a converged state (0) and a non-zero one cannot be normalised (inf)."""
+    if den > 0.0:
+        return num / den
+    return 0.0 if num == 0.0 else np.inf
+
+
 def _fdd_step(u, Ebar_f, T0, lam, mu, qa, qb, G, mats):
     """One evaluation of the fixed-point map u_check -> u_check + G_H (T_check q^b) (Sec. 5.2).
 
@@ -422,7 +430,7 @@ def solve(lam, mu, scheme, E_macro, tol=1e-8, maxit=1000, disc="TD", h=1.0, ref=
         it += 1
         eps, T, Tc, Tq, du = _fdd_step(u, Ebar_f, T0, lam, mu, qa, qb, G, mats)
         T0n = np.sqrt(np.sum(np.abs(Tc[(slice(None), slice(None)) + k0]) ** 2))
-        eta = np.sqrt(np.sum(np.abs(Tq) ** 2)) / T0n
+        eta = _ratio(np.sqrt(np.sum(np.abs(Tq) ** 2)), T0n)
         if stop_rule == 1:
             crit = np.inf if du_prev is None else np.sum(np.sqrt(np.sum(np.abs(du - du_prev) ** 2, axis=0)))
         else:
@@ -483,7 +491,7 @@ def _solve_dgo(lam, mu, T0, Ebar, N, h, lam_h, mu_h, tol, maxit, dgo_m, dgo_tabl
             tau = stiffness_apply(lam - lam_h, mu - mu_h, eps)
             Ec_new = dgo_apply(Gc, forward3(tau, mats))
             dE = Ec_new - Ec
-        eta = np.sqrt(np.sum(np.abs(dE) ** 2)) / enorm
+        eta = _ratio(np.sqrt(np.sum(np.abs(dE) ** 2)), enorm)
         history.append(eta)
         converged = eta < tol
         stop = (it >= max_iters_exact) if max_iters_exact is not None else (converged or it >= maxit)

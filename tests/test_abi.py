@@ -48,6 +48,8 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
     # argument validation happens before any device call
     h = ctypes.c_void_p()
     assert L.gfp_create_grid(5, 8, 8, 1.0, None, ctypes.byref(h)) == -2
+    assert L.gfp_create_grid(8, 1536, 8, 1.0, None, ctypes.byref(h)) == -2   # 2^9 3, above the 1024 limit
+    assert L.gfp_create_grid(8, 8, 2048, 1.0, None, ctypes.byref(h)) == -2
     assert L.gfp_create_grid(0, 8, 8, 1.0, None, ctypes.byref(h)) == -1
     assert L.gfp_create_grid(8, 8, 8, -1.0, None, ctypes.byref(h)) == -1
 

@@ -248,3 +248,18 @@ def test_autotuned_tiles_keep_parity(gfp, prec, op, tmp_path):
         r = g.solve(sch, E, 1e-8, 5000)
         ref = O.solve(lam, mu, op, E, tol=1e-9, maxit=5000, disc="PCD")
         assert r.converged and _rel(r.sigma_mean, ref.sigma_mean) <= 1e-6
+
+
+@pytest.mark.parametrize("op,prec", [("AFB_R", "FP64"), ("F", "FP64"), ("DGO", "FP64"), ("AFB_R", "MIXED")])
+def test_zero_load_degenerate(gfp, op, prec):
+    """Zero mean strain, no eigenstrain: the exact solution eps = 0 after the first iteration, as the oracle."""
+    lam, mu = M.random_field(8, 8, 8, seed=3)
+    g = gfp.Grid(8, 8, 8)
+    g.set_phases(lam, mu)
+    r = g.solve(gfp.scheme(op, "PCD", prec), [0.0] * 6, 1e-8, 50)
+    assert r.converged
+    assert np.all(g.strain() == 0.0) and np.all(np.asarray(r.sigma_mean) == 0.0)
+    if prec == "FP64":
+        ref = O.solve(lam, mu, op, [0.0] * 6, tol=1e-8, maxit=50, disc="PCD")
+        assert r.iters == ref.iters == 1
+    g.close()

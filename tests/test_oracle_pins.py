@@ -789,3 +789,13 @@ def test_dgo_printed_weights_diverge_on_two_phase_cube(form, power, grows):
         assert h[-1] == h.min() and h[-1] < 1e-4 * h[0]
         if form == "polarization":
             assert r.converged
+
+
+@pytest.mark.parametrize("scheme", ["AFB_R", "F", "DGO"])
+def test_zero_load_is_solved_in_one_iteration(scheme):
+    """No mean strain and no eigenstrain: the stress is identically zero, which is equilibrium; the solve
+    stops after its first iteration with eps = 0 and residual 0 (a zero reference norm is no division)."""
+    lam, mu = M.random_field(4, 4, 4, seed=1)
+    r = O.solve(lam, mu, scheme, [0.0] * 6, tol=1e-8, maxit=10)
+    assert r.converged and r.iters == 1 and r.residual == 0.0
+    assert np.all(r.eps == 0.0) and np.all(r.sigma_mean == 0.0)
