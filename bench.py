@@ -262,11 +262,14 @@ def run_gfp(args, rank=0, world=1, local=0):
             steady = {"value": world * N * (m["iters"] + m["outer"]) / m["seconds"], "unit": "voxel-iterations/s",
                       "inner_only": world * N * m["iters"] / m["seconds"], "seconds": m["seconds"],
                       "inner": m["iters"], "outer": m["outer"], "tol": 1e-8}
-    # end to end through the C ABI with host buffers: H2D of lambda, mu, K iterations, D2H of the strain
-    eps_host = np.empty((6, n, n, n))
+    # end to end through the C ABI with host buffers: H2D of lambda, mu from pinned host memory, K
+    # iterations, D2H of the strain into pinned host memory
+    lam_pin = torch.from_numpy(np.ascontiguousarray(lam)).pin_memory()
+    mu_pin = torch.from_numpy(np.ascontiguousarray(mu)).pin_memory()
+    eps_host = torch.empty((6, n, n, n), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.set_phases(lam, mu)
+    g.set_phases(lam_pin, mu_pin)
     g.solve(sch, E, 0.0, K)
     g.strain(eps_host)
     t_e2e = max_over_ranks(time.perf_counter() - t0, world)
