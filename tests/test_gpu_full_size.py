@@ -1,7 +1,8 @@
 """Full-size checks (256^3, the benchmark's grid) in the benchmark's launch configuration: mixed
 precision with x-pass tiles of 2 lines, y tiles of 16 columns and the 8-column two-line z-pass.
 The dense-DFT oracle cannot run at this size, so the checks use properties that hold at any size:
-the closed-form response of a laminate, and agreement with the FP64 GPU solve."""
+the closed-form response of a laminate, agreement with the FP64 GPU solve, and the equilibrium residual
+of the returned strain recomputed on the host with numpy's FFT and the oracle's wave vectors."""
 import numpy as np
 import pytest
 
@@ -133,3 +134,40 @@ def test_random_spheres_512_mixed_matches_fp64(gfp):
     assert r64.converged
     assert _rel(rm.sigma_mean, r64.sigma_mean) <= 1e-6
     g.close()
+
+
+def test_bench_cell_256_equilibrium_residual_independent(gfp):
+    """The benchmark's 256^3 cell solved in mixed precision to eta < 1e-8 (bench tiles): its FP64 strain,
+    checked on the host by an independent route -- sigma = C : eps in numpy, numpy's unitary FFT, and the
+    oracle's AFB/R wave vector q^b (eq. EffNumWavConWil3D; moved from the paper's index order to numpy's)
+    -- has the equilibrium residual ||T_check q^b|| / ||T_check(0)||_F that the GPU reported, below 1e-8."""
+    from oracle import gfp_oracle as O
+    n = 256
+    lam, mu = M.random_spheres(n, vf=0.25, rmin=6.0, rmax=16.0, contrast=100.0, seed=0)
+    E = [0.0, 0.0, 0.0, 0.0, 0.0, 1.0]
+    g = gfp.Grid(n, n, n)
+    g.set_phases(lam, mu)
+    g.set_tiles(gfp.MIXED, [2, 16, -8])
+    r = g.solve(gfp.scheme("AFB_R", "PCD", "MIXED"), E, 1e-8, 20000)
+    assert r.converged and r.residual < 1e-8
+    eps = g.strain()
+    g.close()
+    tr = eps[0] + eps[1] + eps[2]
+    _, qb = O.wave_vectors("AFB_R", n, n, n)
+    m = n // 2
+    qb = np.roll(qb, (-m, -m, -m), axis=(1, 2, 3))   # paper index i <-> kappa = i - m; numpy: kappa mod n
+    pairs = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+    Tq = np.zeros((3, n, n, n), dtype=np.complex128)
+    T0 = np.zeros((3, 3))
+    for c, (i, j) in enumerate(pairs):
+        sig = 2.0 * mu * eps[c] + (lam * tr if i == j else 0.0)
+        Tc = np.fft.fftn(sig, norm="ortho")
+        T0[i, j] = T0[j, i] = Tc[0, 0, 0].real
+        Tq[i] += Tc * qb[j]
+        if i != j:
+            Tq[j] += Tc * qb[i]
+        del Tc, sig
+    eta = np.sqrt(np.sum(np.abs(Tq) ** 2)) / np.linalg.norm(T0)
+    assert eta < 1e-8
+    assert abs(eta - r.residual) <= 1e-4 * r.residual
+    np.testing.assert_allclose(eps.reshape(6, -1).mean(axis=1), E, atol=1e-12)
