@@ -587,6 +587,24 @@ def test_paper_increment_stop_rule_runs():
     assert r.converged and r.iters > 2
 
 
+@pytest.mark.parametrize("scheme", ["AFB_R", "ACD"])
+def test_increment_criterion_from_the_displacement_iterates(scheme):
+    """The paper's stopping quantity of iteration k (Algorithms T-3D / P-3D), sum over the modes of
+    |du^(k) - du^(k-1)|, rebuilt from the displacement fields u^p the oracle returns after k - 1, k and
+    k + 1 iterations: du^(k) - du^(k-1) = u_(k+1) - 2 u_k + u_(k-1) in real space, numpy's unitary FFT,
+    the Euclidean norm of each mode's vector, summed (a non-cubic grid with an odd axis)."""
+    lam, mu = M.random_field(5, 4, 6, seed=8)
+    E = [0.01, -0.002, 0.003, 0.001, 0.0, 0.002]
+    ref = O.solve(lam, mu, scheme, E, tol=0.0, maxit=7, stop_rule=1, max_iters_exact=7)
+    assert np.isinf(ref.history[0])
+    disp = {k: O.solve(lam, mu, scheme, E, max_iters_exact=k).disp for k in range(1, 8)}
+    for k in range(2, 7):
+        d2 = disp[k + 1] - 2.0 * disp[k] + disp[k - 1]
+        F = np.fft.fftn(d2, axes=(1, 2, 3), norm="ortho")
+        crit = np.sum(np.sqrt(np.sum(np.abs(F) ** 2, axis=0)))
+        assert abs(crit - ref.history[k - 1]) <= 1e-12 * ref.history[k - 1]
+
+
 # ----------------------------------------------------------------------------- DGO off-axis pins
 def _voigt_stiffness(lam_h, mu_h):
     """6x6 map from tensor components (11,22,33,23,13,12) of a strain to those of lam tr I + 2 mu eps."""
